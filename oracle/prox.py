@@ -1,0 +1,93 @@
+"""prox of gamma R for R = tau TV_iso + chi_C (Eq. 8), by FGP.
+
+The paper solves this prox with the fast gradient projection (FGP) method of
+Beck and Teboulle, "Fast gradient-based algorithms for constrained total
+variation image denoising and deblurring problems" (IEEE TIP 2009), cited in
+Sec. III-A, without restating it.  This module follows that published
+algorithm on the dual variable p = (p_x, p_y):
+
+    x(p)    = P_C(z - lam D^T p)                       lam = gamma * tau
+    p_k     = Pi_B(r_k + (1 / (8 lam)) D x(r_k))        (1/(4 d lam) in d dims)
+    t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+    r_{k+1} = p_k + ((t_k - 1) / t_{k+1}) (p_k - p_{k-1})
+    output  x(p_K)
+
+with r_1 = p_0 = 0, t_1 = 1.  D is the forward difference with a zero
+difference at the last index (Neumann), Pi_B projects each pixel's (p_x, p_y)
+onto the unit disk (isotropic TV), and P_C clamps to the box C = [lo, hi].
+The paper leaves C as "a bounded convex set" (Sec. II); the box is a reading.
+For complex f the reading is a separable prox: Re f and Im f each take this
+prox with their own box.
+
+Pinned by: tau = 0 gives the clamp, constant images, the closed-form
+two-plateau solution, non-expansiveness and a vanishing duality gap
+(tests/test_oracle_prox.py).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def grad2(x):
+    """Forward differences (D_x x, D_y x), zero at the last column / row."""
+    dx = np.zeros_like(x)
+    dy = np.zeros_like(x)
+    dx[:, :-1] = x[:, 1:] - x[:, :-1]
+    dy[:-1, :] = x[1:, :] - x[:-1, :]
+    return dx, dy
+
+
+def grad2_adj(px, py):
+    """D^T (p_x, p_y): the exact adjoint of ``grad2``."""
+    out = np.zeros_like(px)
+    out[:, :-1] -= px[:, :-1]
+    out[:, 1:] += px[:, :-1]
+    out[:-1, :] -= py[:-1, :]
+    out[1:, :] += py[:-1, :]
+    return out
+
+
+def tv_iso(x):
+    """Isotropic TV: sum_n sqrt(sum_d [D_d x]_n^2) (first term of Eq. 8 without tau)."""
+    dx, dy = grad2(x)
+    return float(np.sum(np.sqrt(dx * dx + dy * dy)))
+
+
+def fgp(z, lam, iters, lo=-np.inf, hi=np.inf, return_dual=False):
+    """argmin_{x in [lo,hi]} 1/2 ||x - z||^2 + lam TV_iso(x), by ``iters`` FGP steps."""
+    z = np.asarray(z, dtype=np.float64)
+    if lam <= 0:
+        x = np.clip(z, lo, hi)
+        return (x, (np.zeros_like(z), np.zeros_like(z))) if return_dual else x
+    px_old = np.zeros_like(z)
+    py_old = np.zeros_like(z)
+    rx = np.zeros_like(z)
+    ry = np.zeros_like(z)
+    t = 1.0
+    step = 1.0 / (8.0 * lam)
+    for _ in range(iters):
+        x = np.clip(z - lam * grad2_adj(rx, ry), lo, hi)
+        dx, dy = grad2(x)
+        qx = rx + step * dx
+        qy = ry + step * dy
+        nrm = np.maximum(1.0, np.sqrt(qx * qx + qy * qy))
+        px, py = qx / nrm, qy / nrm
+        t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        beta = (t - 1.0) / t_new
+        rx = px + beta * (px - px_old)
+        ry = py + beta * (py - py_old)
+        px_old, py_old, t = px, py, t_new
+    x = np.clip(z - lam * grad2_adj(px_old, py_old), lo, hi)
+    return (x, (px_old, py_old)) if return_dual else x
+
+
+def prox_R(z, lam, iters, box_re=(0.0, 2.0), box_im=None):
+    """prox of gamma R at z (Eq. 9's outer prox); complex z takes separable Re / Im proxes."""
+    z = np.asarray(z)
+    xr = fgp(z.real, lam, iters, *box_re)
+    if box_im is None:
+        return xr.astype(np.complex128)
+    xi = fgp(z.imag, lam, iters, *box_im)
+    return xr + 1j * xi
