@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of the CISOR hot path on one GB300 (or N independent replicas).
+
+Workload (default): 256 x 256 grid at lambda/8 (FFT padded to 512 x 512), 64
+plane-wave transmitters, 256 receivers on a circle of radius 24 lambda, 10
+seeded random ellipses with contrast up to 1.0 plus 0.05i absorption, 40 dB
+noise.  One step is one relaxed-FISTA iteration (Eqs. 9-11) from a fixed
+state: 64 forward field solves and 64 adjoint field solves (Eq. 13), each from
+a cold start to true relative residual 1e-4, sensing and adjoint sensing, the
+gradient (Prop. 1), the FGP TV prox and the momentum update.  The metric
+counts LS field solves (forward + adjoint) per second.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LS field solves/s at residual 1e-4, learned vs cold start; % of HBM peak"
+UNIT = "solves/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cisor", choices=["cisor", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _state0(f_true):
+    """Fixed starting point of the timed step: 0.9 x the phantom (inside the box)."""
+    s0 = 0.9 * f_true
+    return np.ascontiguousarray(s0, dtype=np.complex64)
+
+
+def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
+    """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds)."""
+    from oracle import model, solve
+    n = cfg["n"]
+    prob = model.Problem(n, cfg["delta"], angles[list(txs)], rx)
+    apply = lambda v: prob.A(f_point, v.reshape(n, n)).ravel()
+    t0 = time.perf_counter()
+    for t in range(len(txs)):
+        solve.bicgstab(apply, prob.u_in[t].ravel(), prob.u_in[t].ravel(), tol, 20000)
+    return len(txs), time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_1708_01663_gb300 import synth
+    cfg, f_true, angles, rx = synth.make_inputs(args.config)
+    s0 = _state0(f_true).astype(np.complex128)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = k % cfg["T"]
+        nsolve, sec = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
+        if k >= args.warmup:
+            times.append(sec)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: 256x256 lambda/8, P=512, 64 Tx, 256 Rx, contrast<=1+0.05i",
+                   "sample": "one cold-start forward field solve per step (transmitter k mod 64)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 numpy BiCGSTAB, one transmitter per step, cold start to 1e-4"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _traffic_summary():
+    """ncu DRAM bytes per matvec pass from profiles/, valid only for the current conv.cu."""
+    path = os.path.join(ROOT, "profiles", "conv_matvec_c2.md")
+    src = os.path.join(ROOT, "paper_1708_01663_gb300", "csrc", "conv.cu")
+    try:
+        with open(src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+        with open(path) as fh:
+            text = fh.read()
+        vals = {}
+        for line in text.splitlines():
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+        if vals.get("conv_cu_sha256_16") != h:
+            return None
+        return float(vals["dram_bytes_per_pass"])
+    except Exception:
+        return None
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = _dist()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1708_01663_gb300 import build, cisor, synth
+    build.build()
+    dev = torch.device("cuda", local)
+    cfg, f_true, angles, rx = synth.make_inputs(args.config)
+    n, T, M = cfg["n"], cfg["T"], cfg["M"]
+    complex_f = cfg["imag"] != 0.0
+    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f)
+
+    # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
+    f_dev = torch.from_numpy(np.ascontiguousarray(f_true, dtype=np.complex64)).to(dev)
+    y_dev = torch.empty((T, M), dtype=torch.complex64, device=dev)
+    ctx.forward(f_dev, y_out=y_dev, tol=1e-6, max_iter=args.max_iter, check=False)
+    torch.cuda.synchronize()
+    noise = torch.from_numpy(synth.complex_noise(cfg["seed"] + 100, (T, M)).astype(np.complex64)).to(dev)
+    sigma = float(torch.linalg.vector_norm(y_dev)) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(T * M)
+    y_dev += sigma * noise
+    Hh = np.empty((M, n * n), np.complex64)
+    ctx.sensing_matrix(Hh)
+    gamma = 1.0 / (T * float(np.sum(np.abs(Hh.astype(np.complex128)) ** 2)))  # L_Born <= T ||H||_F^2
+    del Hh
+
+    s0 = torch.from_numpy(_state0(f_true)).to(dev)
+    f_st = torch.empty_like(s0)
+    s_st = torch.empty_like(s0)
+    state = ctx.new_state(f_st, s_st, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0, 0.0, 0.5)
+
+    infos = []
+
+    def step(st, y, f_buf, s_buf):
+        f_buf.copy_(s0) if hasattr(f_buf, "copy_") else None
+        s_buf.copy_(s0) if hasattr(s_buf, "copy_") else None
+        st.t, st.k = 1.0, 1
+        _, info = ctx.step(st, y, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
+        infos.append(info.as_dict())
+
+    for _ in range(args.warmup):
+        step(state, y_dev, f_st, s_st)
+    torch.cuda.synchronize()
+    infos.clear()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = ctx.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step(state, y_dev, f_st, s_st)
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_infos = list(infos)
+    solves_per_step = 2 * T
+    value = ws * solves_per_step * args.steps / (ms / 1e3)
+
+    # end to end through host (pinned) buffers: H2D of y and the state, D2H of the new state
+    y_h = torch.empty((T, M), dtype=torch.complex64, pin_memory=True)
+    y_h.copy_(y_dev.cpu())
+    s0_h = s0.cpu()
+    f_h = torch.empty_like(s0_h).pin_memory()
+    s_h = torch.empty_like(s0_h).pin_memory()
+    st_h = ctx.new_state(f_h, s_h, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0, 0.0, 0.5)
+
+    def step_h():
+        f_h.copy_(s0_h)
+        s_h.copy_(s0_h)
+        st_h.t, st_h.k = 1.0, 1
+        ctx.step(st_h, y_h, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
+
+    step_h()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_h()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * solves_per_step * args.steps / e2e_s
+    h2d = y_h.numel() * 8 + 2 * s0_h.numel() * 8
+    d2h = 2 * s0_h.numel() * 8
+
+    # roofline of the dominant kernel chain: one batched FFT matvec over all T transmitters
+    mv_ms = ctx.time_matvec(s0, adjoint=False, reps=20)
+    N = n * n
+    alg_bytes = T * 16 * N + 8 * N
+    achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic_summary()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        s0n = _state0(f_true).astype(np.complex128)
+        nsolve, sec = _oracle_sample_solves(cfg, s0n, angles, rx, [0, 1], args.tol)
+        cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsolve} cold-start forward solves (transmitters 0-1 of {T}) to residual "
+                         f"{args.tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"}
+
+    if rank == 0:
+        it_f = [i["iters_mean"] for i in step_infos]
+        it_a = [i["adj_iters_mean"] for i in step_infos]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: 256x256 grid at lambda/8, FFT 512x512, {T} Tx, {M} Rx, "
+                                   "10 ellipses contrast<=1.0+0.05i, 40 dB",
+                       "step": "one relaxed-FISTA iteration from a fixed state: T forward + T adjoint "
+                               "cold-start solves to residual 1e-4, sensing, gradient, FGP prox (20 it)",
+                       "solves_per_step": solves_per_step, "start": "cold (u_in / 0)",
+                       "l2": "working set > L2 (Krylov vectors 12 x 32 MB)",
+                       "parallelism": "independent replicas" if ws > 1 else "single GPU",
+                       "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
+                       "adj_iters_mean": float(np.mean(it_a)) if it_a else None,
+                       "resid_max": max(i["resid_max"] for i in step_infos) if step_infos else None,
+                       "not_converged": sum(i["n_not_converged"] for i in step_infos)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)",
+                         "ms_per_launch": mv_ms, "alg_bytes_per_launch": alg_bytes,
+                         "peak_kind": f"{peak_kind} (copy bandwidth)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

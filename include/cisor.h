@@ -1,0 +1,180 @@
+/*
+ * cisor.h -- C ABI of the GB300 (sm_103a) hot path of CISOR.
+ *
+ * CISOR (Ma, Mansour, Liu, Boufounos, Kamilov, "Accelerated Image
+ * Reconstruction for Nonlinear Diffractive Imaging", arXiv:1708.01663)
+ * estimates a permittivity contrast f from scattered fields
+ *     y_t = H diag(u_t) f + e_t,     u_t = u_in,t + G diag(f) u_t      (Sec. II, Eqs. 2-3)
+ * by relaxed FISTA (Sec. III-A, Eqs. 9-11) on D(f) + R(f) (Eqs. 6-8), with
+ * the gradient of D from the adjoint-state formula of Prop. 1 (Eqs. 12-13).
+ *
+ * Conventions for every entry point:
+ *  - complex arrays are interleaved complex64 (float re, float im), row-major
+ *    with the x index fastest; fields are transmitter-major [T, n, n];
+ *  - array arguments may be device or host pointers: inputs are copied into
+ *    the context's device buffers and results out of them with
+ *    cudaMemcpyDefault (unified addressing); a call that writes host memory
+ *    returns after the data is there;
+ *  - the caller owns every array it passes; the context owns its tables
+ *    (G spectrum, H, incident fields) and all workspace;
+ *  - work is ordered after prior work on the stream given to cisor_create,
+ *    and later work on that stream is ordered after it; host scalar outputs
+ *    (D, solve info) synchronise that stream;
+ *  - no C++ exception crosses this ABI; on error the status is returned and
+ *    cisor_last_error() describes it (thread-local).  A CUDA error leaves the
+ *    context unusable (destroy it).
+ * Lengths are in any unit shared by delta, wavelength and the positions.
+ */
+#ifndef CISOR_H
+#define CISOR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CISOR_OK = 0,
+  CISOR_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported grid */
+  CISOR_ERR_NOT_CONVERGED = 2, /* a field solve hit max_iter; outputs still written */
+  CISOR_ERR_BREAKDOWN = 3,     /* a Krylov scalar vanished; outputs still written */
+  CISOR_ERR_OOM = 4,           /* device allocation failed */
+  CISOR_ERR_CUDA = 5           /* other CUDA error */
+} cisor_status;
+
+typedef struct cisor_ctx cisor_ctx;
+
+/* Geometry of one imaging set-up (Sec. II and Appendix A, grid).
+ * Pixel l = 1..n of each axis sits at (l - n/2 - 0.5) * delta.  Transmitters
+ * are plane waves exp(j k_b (cos a_t x + sin a_t y)); receivers are points
+ * outside the grid. */
+typedef struct {
+  int dim;                  /* 2 (the scalar 2D model) */
+  int n;                    /* grid side, 8 <= n <= 256; N = n*n pixels */
+  double delta;             /* pixel size */
+  double wavelength;        /* vacuum wavelength; k = 2 pi / wavelength */
+  double eps_b;             /* background permittivity; k_b = k sqrt(eps_b) */
+  int T;                    /* transmitters, 1 <= T <= 1024 */
+  const double* tx_angles;  /* host [T] plane-wave propagation angles, radians */
+  int M;                    /* receivers, 1 <= M */
+  const double* rx_pos;     /* host [M, 2] receiver positions (x, y) */
+  int complex_f;            /* 0: f real (Im f is neither updated nor regularised); 1: complex f */
+  int pad;                  /* FFT side P >= 2n - 1, a power of two <= 512; 0 = smallest such */
+} cisor_geometry;
+
+/* Options of the field solves A u = u_in and A^H v = b (Eq. 13). */
+typedef struct {
+  double tol;     /* stop when the true relative residual ||b - A x|| / ||b|| <= tol */
+  int max_iter;   /* BiCGSTAB iteration cap per transmitter */
+  int x0_mode;    /* 0: cold start (u_in for A u = u_in, 0 for the adjoint); 1: x0 argument;
+                     2: previous solution held by the context (cold if none) */
+} cisor_solve_opts;
+
+/* Per-call solve statistics (host struct, filled on return). */
+typedef struct {
+  int iters_max;        /* max BiCGSTAB iterations over transmitters (forward solve) */
+  double iters_mean;
+  double resid_max;     /* max true relative residual at exit */
+  int n_not_converged;
+  int adj_iters_max;    /* same for the adjoint solve (cisor_grad / cisor_step) */
+  double adj_iters_mean;
+  double adj_resid_max;
+} cisor_solve_info;
+
+/* Relaxed-FISTA state (Eqs. 9-11).  f and s are caller-owned [N] complex64
+ * arrays; on entry f = f_{k-1}, s = s_k, t = t_k; on return f = f_k,
+ * s = s_{k+1}, t = t_{k+1}, k incremented.  Start with f = s = f_0, t = 1, k = 1. */
+typedef struct {
+  void* f;
+  void* s;
+  double t;
+  int k;
+  double alpha;     /* relaxation, 0 <= alpha < 1 (0.96 in Sec. IV) */
+  double gamma;     /* step size, 0 < gamma <= (1 - alpha^2) / (2 L) (Prop. 3) */
+  double tau;       /* TV weight (Eq. 8) */
+  int tv_iters;     /* FGP iterations of the prox */
+  double lo, hi;    /* box C for Re f */
+  double lo_im, hi_im; /* box C for Im f (complex_f only) */
+  double D;         /* out: D(s_k) of Eq. 7 */
+} cisor_fista_state;
+
+/* Build the tables of a geometry on the current CUDA device: the spectrum of
+ * the circulant embedding of G (Eq. 3, FP64, then stored complex64), H (Eq. 2),
+ * incident fields, and the solver workspace.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  On success *out owns all of it. */
+cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* geom, void* stream);
+
+/* Free a context (NULL is a no-op). */
+cisor_status cisor_destroy(cisor_ctx* ctx);
+
+/* Grid size actually used: writes n, P, T, M, N (any pointer may be NULL). */
+cisor_status cisor_sizes(const cisor_ctx* ctx, int* n, int* P, int* T, int* M, long long* N);
+
+/* Copy out the unscaled spectrum ghat = FFT_P(c) of the circulant embedding
+ * of G (Eq. 3 through Sec. III-A's FFT convolution): [P, P] complex64. */
+cisor_status cisor_green_spectrum(cisor_ctx* ctx, void* ghat_out);
+
+/* Copy out H (Eq. 2): [M, N] complex64. */
+cisor_status cisor_sensing_matrix(cisor_ctx* ctx, void* H_out);
+
+/* Copy out the incident fields u_in: [T, N] complex64. */
+cisor_status cisor_incident(cisor_ctx* ctx, void* u_in_out);
+
+/* y = A x (adjoint = 0) or y = A^H x (adjoint = 1) with A = I - G diag(f)
+ * (Eq. 4), for nvec <= T vectors x, y: [nvec, N] complex64; f: [N]. */
+cisor_status cisor_apply_A(cisor_ctx* ctx, const void* f, const void* x, void* y, int adjoint, int nvec);
+
+/* Forward model (Eqs. 2-3, 13): solve A u_t = u_in,t for every transmitter,
+ * then y_t = H diag(u_t) f.  u_in: [T, N] or NULL (the geometry's plane
+ * waves); x0: [T, N] initial guesses (x0_mode 1) or NULL; u_out: [T, N] or
+ * NULL; y_out: [T, M] or NULL.  The solution is kept for x0_mode 2. */
+cisor_status cisor_forward(cisor_ctx* ctx, const void* f, const void* u_in, const void* x0, void* u_out,
+                           void* y_out, const cisor_solve_opts* opts, cisor_solve_info* info);
+
+/* Z = H diag(u_t) f for all transmitters (Eq. 5): u [T, N], Z_out [T, M]. */
+cisor_status cisor_sense(cisor_ctx* ctx, const void* f, const void* u, void* Z_out);
+
+/* z_t = H^H w_t and b_t = diag(f)^H z_t (right-hand side of Eq. 13):
+ * w [T, M]; z_out, b_out [T, N] (either may be NULL). */
+cisor_status cisor_sense_adjoint(cisor_ctx* ctx, const void* f, const void* w, void* z_out, void* b_out);
+
+/* Data term and gradient (Eq. 7, Prop. 1): D = 1/2 sum_t ||H diag(u_t) f - y_t||^2
+ * and g = sum_t conj(u_t) (H^H w_t + G^H v_t) with A u_t = u_in,t,
+ * A^H v_t = diag(f)^H H^H w_t.  grad_out [N] complex64 receives g: its real
+ * part is grad D for real f; for complex f, (Re g, Im g) are the partial
+ * derivatives in (Re f, Im f).  y: [T, M]; D_out: host double (may be NULL). */
+cisor_status cisor_grad(cisor_ctx* ctx, const void* f, const void* y, void* grad_out, double* D_out,
+                        const cisor_solve_opts* opts, cisor_solve_info* info);
+
+/* x = argmin_{x in C} 1/2 ||x - z||^2 + gamma_tau TV_iso(x) (prox of Eq. 8)
+ * by `iters` FGP iterations (Beck-Teboulle, cited in Sec. III-A), dual cold
+ * start; C is the box [lo, hi] for Re and, for complex_f, [lo_im, hi_im] for
+ * Im (separable prox); for real f Im x = 0.  z, x: [N] complex64. */
+cisor_status cisor_tv_prox(cisor_ctx* ctx, const void* z, void* x, double gamma_tau, int iters, double lo,
+                           double hi, double lo_im, double hi_im);
+
+/* One relaxed-FISTA iteration (Eqs. 9-11) on the state; y: [T, M] measurements.
+ * Inner solves use opts (x0_mode 2 warm-starts from the previous step). */
+cisor_status cisor_step(cisor_ctx* ctx, cisor_fista_state* st, const void* y, const cisor_solve_opts* opts,
+                        cisor_solve_info* info);
+
+/* Number of CUDA kernels this context has launched since creation (kernels
+ * inside replayed CUDA graphs included).  *count is a host long long. */
+cisor_status cisor_launch_count(const cisor_ctx* ctx, long long* count);
+
+/* Time `reps` back-to-back batched matvecs y_t = A x_t (adjoint = 0) or
+ * A^H x_t (adjoint = 1) over all T transmitters of the context's workspace
+ * (the FFT-convolution kernels of the field solves, Eq. 4), with CUDA events
+ * on the context's stream, after one untimed pass.  *ms_per_pass receives
+ * the mean milliseconds of one pass.  f: [N] complex64, as in cisor_apply_A. */
+cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int reps, double* ms_per_pass);
+
+/* Last error message of this thread ("" if none). */
+const char* cisor_last_error(void);
+
+/* Library version string. */
+const char* cisor_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CISOR_H */

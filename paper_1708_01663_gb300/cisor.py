@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libcisor (include/cisor.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts arrays to
+pointers and structs.  Arrays may be torch tensors (CUDA or CPU) or numpy
+arrays; complex arrays must be contiguous complex64.  Outputs are caller
+allocated.  Loading fails loudly when libcisor.so has not been built: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcisor.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cisor.h")
+
+OK, ERR_INVALID_ARG, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_OOM, ERR_CUDA = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "BREAKDOWN", 4: "OOM", 5: "CUDA"}
+
+
+class Geometry(Structure):
+    _fields_ = [("dim", c_int), ("n", c_int), ("delta", c_double), ("wavelength", c_double),
+                ("eps_b", c_double), ("T", c_int), ("tx_angles", POINTER(c_double)), ("M", c_int),
+                ("rx_pos", POINTER(c_double)), ("complex_f", c_int), ("pad", c_int)]
+
+
+class SolveOpts(Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int), ("x0_mode", c_int)]
+
+
+class SolveInfo(Structure):
+    _fields_ = [("iters_max", c_int), ("iters_mean", c_double), ("resid_max", c_double),
+                ("n_not_converged", c_int), ("adj_iters_max", c_int), ("adj_iters_mean", c_double),
+                ("adj_resid_max", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FistaState(Structure):
+    _fields_ = [("f", c_void_p), ("s", c_void_p), ("t", c_double), ("k", c_int), ("alpha", c_double),
+                ("gamma", c_double), ("tau", c_double), ("tv_iters", c_int), ("lo", c_double),
+                ("hi", c_double), ("lo_im", c_double), ("hi_im", c_double), ("D", c_double)]
+
+
+class CisorError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cisor status {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def declared_functions():
+    """Names of the entry points declared in include/cisor.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const char\*|cisor_status)\s+(cisor_\w+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libcisor.so and declare the signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1708_01663_gb300.build.build() "
+                           "(the CUDA path has no fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i, d = c_void_p, c_int, c_double
+    sig = {
+        "cisor_create": [POINTER(c_void_p), POINTER(Geometry), vp],
+        "cisor_destroy": [vp],
+        "cisor_sizes": [vp, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_longlong)],
+        "cisor_green_spectrum": [vp, vp],
+        "cisor_sensing_matrix": [vp, vp],
+        "cisor_incident": [vp, vp],
+        "cisor_apply_A": [vp, vp, vp, vp, i, i],
+        "cisor_forward": [vp, vp, vp, vp, vp, vp, POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_sense": [vp, vp, vp, vp],
+        "cisor_sense_adjoint": [vp, vp, vp, vp, vp],
+        "cisor_grad": [vp, vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_tv_prox": [vp, vp, vp, d, i, d, d, d, d],
+        "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_launch_count": [vp, POINTER(c_longlong)],
+        "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = c_int
+    lib.cisor_last_error.restype = c_char_p
+    lib.cisor_last_error.argtypes = []
+    lib.cisor_version.restype = c_char_p
+    lib.cisor_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().cisor_last_error().decode()
+
+
+def _check(status, allow=()):
+    if status != OK and status not in allow:
+        raise CisorError(status, last_error())
+    return status
+
+
+def ptr(a, count=None, dtype="complex64"):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        if str(a.dtype).replace("torch.", "") != dtype:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        if count is not None and a.numel() != count:
+            raise ValueError(f"expected {count} elements, got {a.numel()}")
+        return a.data_ptr()
+    arr = a
+    if not isinstance(arr, np.ndarray) or not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be a contiguous numpy array or torch tensor")
+    if arr.dtype != np.dtype(dtype):
+        raise TypeError(f"expected {dtype}, got {arr.dtype}")
+    if count is not None and arr.size != count:
+        raise ValueError(f"expected {count} elements, got {arr.size}")
+    return arr.ctypes.data
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Cisor:
+    """One imaging geometry: tables and workspace on the current CUDA device."""
+
+    def __init__(self, n, delta, tx_angles, rx_pos, wavelength=1.0, eps_b=1.0, complex_f=False, pad=0,
+                 stream=None):
+        lib = load()
+        self._lib = lib
+        self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64)
+        self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, 2)
+        g = Geometry(2, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
+                     self._ang.ctypes.data_as(POINTER(c_double)), len(self._rx),
+                     self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad))
+        self._ctx = c_void_p()
+        self.stream = _current_stream() if stream is None else stream
+        _check(lib.cisor_create(ctypes.byref(self._ctx), ctypes.byref(g), self.stream))
+        n_, P, T, M, N = c_int(), c_int(), c_int(), c_int(), c_longlong()
+        _check(lib.cisor_sizes(self._ctx, ctypes.byref(n_), ctypes.byref(P), ctypes.byref(T), ctypes.byref(M),
+                               ctypes.byref(N)))
+        self.n, self.P, self.T, self.M, self.N = n_.value, P.value, T.value, M.value, N.value
+        self.complex_f = bool(complex_f)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.cisor_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----- tables
+    def green_spectrum(self, out):
+        return _check(self._lib.cisor_green_spectrum(self._ctx, ptr(out, self.P * self.P)))
+
+    def sensing_matrix(self, out):
+        return _check(self._lib.cisor_sensing_matrix(self._ctx, ptr(out, self.M * self.N)))
+
+    def incident(self, out):
+        return _check(self._lib.cisor_incident(self._ctx, ptr(out, self.T * self.N)))
+
+    # ----- operators
+    def apply_A(self, f, x, y, adjoint=False):
+        nvec = (x.numel() if hasattr(x, "numel") else x.size) // self.N
+        return _check(self._lib.cisor_apply_A(self._ctx, ptr(f, self.N), ptr(x, nvec * self.N),
+                                              ptr(y, nvec * self.N), 1 if adjoint else 0, nvec))
+
+    def sense(self, f, u, Z):
+        return _check(self._lib.cisor_sense(self._ctx, ptr(f, self.N), ptr(u, self.T * self.N),
+                                            ptr(Z, self.T * self.M)))
+
+    def sense_adjoint(self, f, w, z=None, b=None):
+        return _check(self._lib.cisor_sense_adjoint(self._ctx, ptr(f, self.N), ptr(w, self.T * self.M),
+                                                    ptr(z, self.T * self.N), ptr(b, self.T * self.N)))
+
+    # ----- solves and gradient
+    def forward(self, f, u_in=None, x0=None, u_out=None, y_out=None, tol=1e-4, max_iter=2000, x0_mode=0,
+                check=True):
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        info = SolveInfo()
+        st = self._lib.cisor_forward(self._ctx, ptr(f, self.N), ptr(u_in, self.T * self.N),
+                                     ptr(x0, self.T * self.N), ptr(u_out, self.T * self.N),
+                                     ptr(y_out, self.T * self.M), ctypes.byref(opts), ctypes.byref(info))
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return st, info
+
+    def grad(self, f, y, grad_out, tol=1e-4, max_iter=2000, x0_mode=0, check=True):
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        info = SolveInfo()
+        D = c_double()
+        st = self._lib.cisor_grad(self._ctx, ptr(f, self.N), ptr(y, self.T * self.M), ptr(grad_out, self.N),
+                                  ctypes.byref(D), ctypes.byref(opts), ctypes.byref(info))
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return D.value, st, info
+
+    def tv_prox(self, z, x, gamma_tau, iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5):
+        return _check(self._lib.cisor_tv_prox(self._ctx, ptr(z, self.N), ptr(x, self.N), float(gamma_tau),
+                                              int(iters), float(lo), float(hi), float(lo_im), float(hi_im)))
+
+    def new_state(self, f, s, alpha, gamma, tau, tv_iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5):
+        """Relaxed-FISTA state over caller-owned f and s arrays (t = 1, k = 1)."""
+        st = FistaState(ptr(f, self.N), ptr(s, self.N), 1.0, 1, alpha, gamma, tau, tv_iters, lo, hi, lo_im, hi_im,
+                        0.0)
+        st._keep = (f, s)
+        return st
+
+    def launch_count(self):
+        v = c_longlong()
+        _check(self._lib.cisor_launch_count(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    def time_matvec(self, f, adjoint=False, reps=20):
+        ms = c_double()
+        _check(self._lib.cisor_time_matvec(self._ctx, ptr(f, self.N), 1 if adjoint else 0, int(reps),
+                                           ctypes.byref(ms)))
+        return ms.value
+
+    def step(self, state, y, tol=1e-4, max_iter=2000, x0_mode=2, check=True):
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        info = SolveInfo()
+        st = self._lib.cisor_step(self._ctx, ctypes.byref(state), ptr(y, self.T * self.M), ctypes.byref(opts),
+                                  ctypes.byref(info))
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return st, info

@@ -1,0 +1,561 @@
+// C ABI entry points (include/cisor.h).  Arguments are copied into the
+// context's device buffers with cudaMemcpyDefault (unified addressing: host
+// or device pointers), work runs on the context's own non-blocking stream,
+// ordered after and before the caller's stream with events, and results are
+// copied out; a call that writes host memory synchronises before returning.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+namespace cisor {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+cisor_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what, file, line);
+  return e == cudaErrorMemoryAllocation ? CISOR_ERR_OOM : CISOR_ERR_CUDA;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__global__ void scale_copy_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long n, float s) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2(in[i].x * s, in[i].y * s);
+}
+
+// Orders the call after the caller's stream on entry and the caller's stream
+// after the call on exit; synchronises if host memory was written.
+struct Call {
+  cisor_ctx* c;
+  bool host_out = false;
+  explicit Call(cisor_ctx* ctx) : c(ctx) {}
+  cisor_status enter() {
+    CISOR_CUDA(cudaEventRecord(c->ev_a, c->user_stream));
+    CISOR_CUDA(cudaStreamWaitEvent(c->stream, c->ev_a, 0));
+    return CISOR_OK;
+  }
+  cisor_status in(void* dst, const void* src, size_t bytes) {
+    CISOR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return CISOR_OK;
+  }
+  cisor_status out(void* dst, const void* src, size_t bytes) {
+    if (!dst) return CISOR_OK;
+    if (!is_device_ptr(dst)) host_out = true;
+    CISOR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return CISOR_OK;
+  }
+  cisor_status leave() {
+    CISOR_CUDA(cudaEventRecord(c->ev_b, c->stream));
+    CISOR_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_b, 0));
+    if (host_out) CISOR_CUDA(cudaStreamSynchronize(c->stream));
+    return CISOR_OK;
+  }
+};
+
+static bool check_opts(const cisor_solve_opts* o) {
+  if (!o) {
+    set_error("solve options are NULL");
+    return false;
+  }
+  if (!(o->tol > 0.0) || o->max_iter < 1 || o->x0_mode < 0 || o->x0_mode > 2) {
+    set_error("invalid solve options (tol %g, max_iter %d, x0_mode %d)", o->tol, o->max_iter, o->x0_mode);
+    return false;
+  }
+  return true;
+}
+
+static cisor_status worse(cisor_status a, cisor_status b) {
+  if (a == CISOR_ERR_CUDA || b == CISOR_ERR_CUDA || a == CISOR_ERR_OOM || b == CISOR_ERR_OOM)
+    return (a == CISOR_ERR_CUDA || a == CISOR_ERR_OOM) ? a : b;
+  if (a == CISOR_ERR_BREAKDOWN || b == CISOR_ERR_BREAKDOWN) return CISOR_ERR_BREAKDOWN;
+  if (a == CISOR_ERR_NOT_CONVERGED || b == CISOR_ERR_NOT_CONVERGED) return CISOR_ERR_NOT_CONVERGED;
+  return a != CISOR_OK ? a : b;
+}
+
+static bool solve_ok(cisor_status s) {
+  return s == CISOR_OK || s == CISOR_ERR_NOT_CONVERGED || s == CISOR_ERR_BREAKDOWN;
+}
+
+// Gradient machinery on c->f (the point) and c->yobs (the data): forward
+// solve into c->u, w and D, adjoint RHS, adjoint solve into c->vadj,
+// gz = z + G^H v, g = sum_t conj(u_t) gz_t into c->grad and, when zstep is
+// given, zstep = s - gamma g.
+static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s, float2* zstep,
+                              double* D, cisor_solve_info* info) {
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  if (o->x0_mode != 2 || !c->have_u) CISOR_CUDA(cudaMemcpyAsync(c->u, c->u_in, vb, cudaMemcpyDeviceToDevice, c->stream));
+  cisor_solve_info li{};
+  int nb1 = 0, nb2 = 0;
+  cisor_status s1 = solve_batch(c, 0, c->f, c->u_in, c->u, c->T, o->tol, o->max_iter, &li.iters_max, &li.iters_mean,
+                                &li.resid_max, &nb1);
+  if (!solve_ok(s1)) return s1;
+  c->have_u = 1;
+  CISOR_TRY(residual_and_D(c, c->f, c->u, c->yobs, c->Y, c->w, c->T));
+  CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
+  if (o->x0_mode != 2 || !c->have_v) CISOR_CUDA(cudaMemsetAsync(c->vadj, 0, vb, c->stream));
+  cisor_status s2 = solve_batch(c, 1, c->f, c->b, c->vadj, c->T, o->tol, o->max_iter, &li.adj_iters_max,
+                                &li.adj_iters_mean, &li.adj_resid_max, &nb2);
+  if (!solve_ok(s2)) return s2;
+  c->have_v = 1;
+  li.n_not_converged = nb1 + nb2;
+  ConvOp op{};
+  op.adjoint = 1;
+  op.mul_f = 0;
+  op.prologue = PRO_COPY;
+  op.src = c->vadj;
+  op.epilogue = EPI_CONV_ADD;
+  op.aux = c->z;
+  op.out = c->gz;
+  op.f = c->f;
+  op.ntx = c->T;
+  CISOR_TRY(conv_pass(c, op));
+  CISOR_TRY(grad_assemble(c, c->u, c->gz, s, gamma, c->grad, zstep, c->T));
+  CISOR_CUDA(cudaMemcpyAsync(c->h_dsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  if (D) *D = c->h_dsum[0];
+  if (info) *info = li;
+  return worse(s1, s2);
+}
+
+static void free_ctx(cisor_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+  void* dev[] = {c->ghat, c->tw, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
+                 c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
+                 c->part, c->scal, c->active, c->iters, c->txflag, c->n_active, c->dsum, c->sparams, c->tv_z,
+                 c->tv_r0, c->tv_r1, c->tv_p};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (c->h_n_active) cudaFreeHost(c->h_n_active);
+  if (c->h_dsum) cudaFreeHost(c->h_dsum);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace cisor
+
+using namespace cisor;
+
+extern "C" {
+
+const char* cisor_last_error(void) { return g_err; }
+
+const char* cisor_version(void) { return "cisor-gb300 0.1 (sm_103a)"; }
+
+cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream) {
+  if (!out || !g) {
+    set_error("cisor_create: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (g->dim != 2) {
+    set_error("only dim = 2 is supported (got %d)", g->dim);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (g->n < 8 || g->n > 256 || !(g->delta > 0) || !(g->wavelength > 0) || !(g->eps_b > 0) || g->T < 1 ||
+      g->T > 1024 || g->M < 1 || !g->tx_angles || !g->rx_pos) {
+    set_error("invalid geometry (n %d, T %d, M %d, delta %g, wavelength %g, eps_b %g)", g->n, g->T, g->M, g->delta,
+              g->wavelength, g->eps_b);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  int P = g->pad;
+  if (P == 0) {
+    P = 64;
+    while (P < 2 * g->n - 1) P *= 2;
+  }
+  if ((P & (P - 1)) != 0 || P < 64 || P > 512 || P < 2 * g->n - 1) {
+    set_error("FFT side %d must be a power of two in [64, 512] and >= 2n - 1 = %d", P, 2 * g->n - 1);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  cisor_ctx* c = new (std::nothrow) cisor_ctx();
+  if (!c) {
+    set_error("out of host memory");
+    return CISOR_ERR_OOM;
+  }
+  c->dim = 2;
+  c->n = g->n;
+  c->P = P;
+  c->T = g->T;
+  c->M = g->M;
+  c->complex_f = g->complex_f ? 1 : 0;
+  c->N = (long long)g->n * g->n;
+  c->delta = g->delta;
+  c->wavelength = g->wavelength;
+  c->eps_b = g->eps_b;
+  c->k = 2.0 * 3.14159265358979323846 / g->wavelength;
+  c->kb = c->k * sqrt(g->eps_b);
+  c->tx_angles.assign(g->tx_angles, g->tx_angles + g->T);
+  c->rx_pos.assign(g->rx_pos, g->rx_pos + 2 * g->M);
+  c->user_stream = (cudaStream_t)stream;
+  c->graph_chunk = 4;
+  const int RB = conv_rows_per_block(P);
+  c->nblk = (c->n + RB - 1) / RB;
+  {
+    const int tiles = ((c->M + 63) / 64) * ((c->T + 31) / 32);
+    int ks = (2 * 152 + tiles - 1) / tiles;
+    const int kmax = (int)((c->N + 255) / 256);
+    c->ksplit = ks < 1 ? 1 : (ks > kmax ? kmax : ks);
+  }
+  cisor_status st = CISOR_OK;
+  auto fail = [&](cisor_status s) {
+    free_ctx(c);
+    return s;
+  };
+#define ALLOC(ptr, bytes)                                              \
+  do {                                                                 \
+    cudaError_t e__ = cudaMalloc((void**)&(ptr), (bytes));             \
+    if (e__ != cudaSuccess) return fail(cuda_fail(e__, "cudaMalloc " #ptr, __FILE__, __LINE__)); \
+  } while (0)
+  {
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "stream/event setup", __FILE__, __LINE__));
+  }
+  const size_t TN = (size_t)c->T * c->N * sizeof(float2);
+  const size_t Nb = (size_t)c->N * sizeof(float2);
+  const size_t TM = (size_t)c->T * c->M * sizeof(float2);
+  ALLOC(c->ghat, sizeof(float2) * P * P);
+  ALLOC(c->tw, sizeof(float2) * P);
+  ALLOC(c->H, (size_t)c->M * c->N * sizeof(float2));
+  ALLOC(c->u_in, TN);
+  ALLOC(c->R, (size_t)c->T * c->n * P * sizeof(float2));
+  ALLOC(c->r, TN);
+  ALLOC(c->rhat, TN);
+  ALLOC(c->p, TN);
+  ALLOC(c->v, TN);
+  ALLOC(c->s, TN);
+  ALLOC(c->tv, TN > sizeof(float2) * P * P ? TN : sizeof(float2) * P * P);
+  ALLOC(c->b, TN);
+  ALLOC(c->u, TN);
+  ALLOC(c->vadj, TN);
+  ALLOC(c->z, TN);
+  ALLOC(c->gz, TN);
+  ALLOC(c->f, Nb);
+  ALLOC(c->fz, Nb);
+  ALLOC(c->grad, Nb);
+  ALLOC(c->work_n, Nb);
+  ALLOC(c->Y, TM);
+  ALLOC(c->w, TM);
+  ALLOC(c->yobs, TM);
+  ALLOC(c->sense_part, TM * c->ksplit);
+  ALLOC(c->part, sizeof(double) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk);
+  ALLOC(c->scal, sizeof(double) * 2 * SC_STRIDE * (size_t)c->T);
+  ALLOC(c->active, sizeof(int) * c->T);
+  ALLOC(c->iters, sizeof(int) * c->T);
+  ALLOC(c->txflag, sizeof(int) * c->T);
+  ALLOC(c->n_active, sizeof(int));
+  ALLOC(c->dsum, sizeof(double) * 4);
+  ALLOC(c->sparams, sizeof(double) * 2);
+  ALLOC(c->tv_z, sizeof(float) * 2 * c->N);
+  ALLOC(c->tv_r0, sizeof(float) * 4 * c->N);
+  ALLOC(c->tv_r1, sizeof(float) * 4 * c->N);
+  ALLOC(c->tv_p, sizeof(float) * 4 * c->N);
+#undef ALLOC
+  {
+    cudaError_t e = cudaMallocHost((void**)&c->h_n_active, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_dsum, sizeof(double) * 4);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__));
+  }
+  st = conv_init(P);
+  if (st != CISOR_OK) return fail(st);
+  st = build_tables(c);
+  if (st != CISOR_OK) return fail(st);
+  *out = c;
+  return CISOR_OK;
+}
+
+cisor_status cisor_destroy(cisor_ctx* ctx) {
+  free_ctx(ctx);
+  return CISOR_OK;
+}
+
+cisor_status cisor_sizes(const cisor_ctx* c, int* n, int* P, int* T, int* M, long long* N) {
+  if (!c) {
+    set_error("NULL context");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (n) *n = c->n;
+  if (P) *P = c->P;
+  if (T) *T = c->T;
+  if (M) *M = c->M;
+  if (N) *N = c->N;
+  return CISOR_OK;
+}
+
+cisor_status cisor_green_spectrum(cisor_ctx* c, void* out) {
+  if (!c || !out) {
+    set_error("cisor_green_spectrum: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  const long long PP = (long long)c->P * c->P;
+  scale_copy_kernel<<<(unsigned)((PP + 255) / 256), 256, 0, c->stream>>>(c->ghat, c->tv, PP, (float)PP);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  CISOR_TRY(call.out(out, c->tv, sizeof(float2) * PP));
+  return call.leave();
+}
+
+cisor_status cisor_sensing_matrix(cisor_ctx* c, void* out) {
+  if (!c || !out) {
+    set_error("cisor_sensing_matrix: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.out(out, c->H, sizeof(float2) * (size_t)c->M * c->N));
+  return call.leave();
+}
+
+cisor_status cisor_incident(cisor_ctx* c, void* out) {
+  if (!c || !out) {
+    set_error("cisor_incident: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.out(out, c->u_in, sizeof(float2) * (size_t)c->T * c->N));
+  return call.leave();
+}
+
+cisor_status cisor_apply_A(cisor_ctx* c, const void* f, const void* x, void* y, int adjoint, int nvec) {
+  if (!c || !f || !x || !y || nvec < 1 || nvec > (c ? c->T : 0)) {
+    set_error("cisor_apply_A: NULL argument or nvec outside [1, T]");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  const size_t vb = sizeof(float2) * (size_t)nvec * c->N;
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_TRY(call.in(c->s, x, vb));
+  ConvOp op{};
+  op.adjoint = adjoint ? 1 : 0;
+  op.mul_f = 1;
+  op.prologue = PRO_COPY;
+  op.src = c->s;
+  op.epilogue = EPI_MATVEC;
+  op.esrc = c->s;
+  op.out = c->tv;
+  op.f = c->f;
+  op.ntx = nvec;
+  CISOR_TRY(conv_pass(c, op));
+  CISOR_TRY(call.out(y, c->tv, vb));
+  return call.leave();
+}
+
+cisor_status cisor_forward(cisor_ctx* c, const void* f, const void* u_in, const void* x0, void* u_out, void* y_out,
+                           const cisor_solve_opts* o, cisor_solve_info* info) {
+  if (!c || !f) {
+    set_error("cisor_forward: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
+  if (o->x0_mode == 1 && !x0) {
+    set_error("cisor_forward: x0_mode 1 needs x0");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  const float2* b = c->u_in;
+  if (u_in) {
+    CISOR_TRY(call.in(c->b, u_in, vb));
+    b = c->b;
+  }
+  if (o->x0_mode == 1) {
+    CISOR_TRY(call.in(c->u, x0, vb));
+  } else if (o->x0_mode == 0 || !c->have_u) {
+    CISOR_CUDA(cudaMemcpyAsync(c->u, b, vb, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  cisor_solve_info li{};
+  int nb = 0;
+  cisor_status st = solve_batch(c, 0, c->f, b, c->u, c->T, o->tol, o->max_iter, &li.iters_max, &li.iters_mean,
+                                &li.resid_max, &nb);
+  if (!solve_ok(st)) return st;
+  li.n_not_converged = nb;
+  c->have_u = 1;
+  if (u_out) CISOR_TRY(call.out(u_out, c->u, vb));
+  if (y_out) {
+    CISOR_TRY(sense_forward(c, c->f, c->u, c->Y, c->T));
+    CISOR_TRY(call.out(y_out, c->Y, sizeof(float2) * (size_t)c->T * c->M));
+  }
+  if (info) *info = li;
+  CISOR_TRY(call.leave());
+  return st;
+}
+
+cisor_status cisor_sense(cisor_ctx* c, const void* f, const void* u, void* Z_out) {
+  if (!c || !f || !u || !Z_out) {
+    set_error("cisor_sense: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_TRY(call.in(c->s, u, sizeof(float2) * (size_t)c->T * c->N));
+  CISOR_TRY(sense_forward(c, c->f, c->s, c->Y, c->T));
+  CISOR_TRY(call.out(Z_out, c->Y, sizeof(float2) * (size_t)c->T * c->M));
+  return call.leave();
+}
+
+cisor_status cisor_sense_adjoint(cisor_ctx* c, const void* f, const void* w, void* z_out, void* b_out) {
+  if (!c || !f || !w) {
+    set_error("cisor_sense_adjoint: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_TRY(call.in(c->w, w, sizeof(float2) * (size_t)c->T * c->M));
+  CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  CISOR_TRY(call.out(z_out, c->z, vb));
+  CISOR_TRY(call.out(b_out, c->b, vb));
+  return call.leave();
+}
+
+cisor_status cisor_grad(cisor_ctx* c, const void* f, const void* y, void* grad_out, double* D_out,
+                        const cisor_solve_opts* o, cisor_solve_info* info) {
+  if (!c || !f || !y || !grad_out) {
+    set_error("cisor_grad: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
+  double D = 0.0;
+  cisor_status st = grad_core(c, o, 0.0, nullptr, nullptr, &D, info);
+  if (!solve_ok(st)) return st;
+  CISOR_TRY(call.out(grad_out, c->grad, sizeof(float2) * c->N));
+  if (D_out) *D_out = D;
+  CISOR_TRY(call.leave());
+  return st;
+}
+
+cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo, double hi,
+                           double lo_im, double hi_im) {
+  if (!c || !z || !x || iters < 0 || !(lo <= hi) || (c && c->complex_f && !(lo_im <= hi_im))) {
+    set_error("cisor_tv_prox: NULL argument, negative iteration count or empty box");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->fz, z, sizeof(float2) * c->N));
+  CISOR_TRY(tv_prox(c, c->fz, c->work_n, gamma_tau, iters, lo, hi, lo_im, hi_im, c->complex_f, nullptr, 0.0, nullptr));
+  CISOR_TRY(call.out(x, c->work_n, sizeof(float2) * c->N));
+  return call.leave();
+}
+
+cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, const cisor_solve_opts* o,
+                        cisor_solve_info* info) {
+  if (!c || !st || !st->f || !st->s || !y) {
+    set_error("cisor_step: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
+  if (!(st->alpha >= 0.0 && st->alpha <= 1.0) || !(st->gamma > 0.0) || !(st->tau >= 0.0) || st->tv_iters < 0 ||
+      !(st->lo <= st->hi) || (c->complex_f && !(st->lo_im <= st->hi_im)) || !(st->t >= 1.0)) {
+    set_error("cisor_step: invalid state (alpha %g, gamma %g, tau %g, t %g)", st->alpha, st->gamma, st->tau, st->t);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  const size_t nb = sizeof(float2) * c->N;
+  CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
+  CISOR_TRY(call.in(c->f, st->s, nb));       // gradient at s_k
+  CISOR_TRY(call.in(c->work_n, st->f, nb));  // f_{k-1}
+  double D = 0.0;
+  cisor_status s1 = grad_core(c, o, st->gamma, c->f, c->fz, &D, info);
+  if (!solve_ok(s1)) return s1;
+  const double t = st->t;
+  const double tn = (sqrt(4.0 * t * t + 1.0) + 1.0) / 2.0;
+  const double beta = st->alpha * (t - 1.0) / tn;
+  // f_k = prox(s_k - gamma grad D(s_k)) into work_n, s_{k+1} into c->f
+  CISOR_TRY(tv_prox(c, c->fz, c->work_n, st->gamma * st->tau, st->tv_iters, st->lo, st->hi, st->lo_im, st->hi_im,
+                    c->complex_f, c->work_n, beta, c->f));
+  CISOR_TRY(call.out(st->f, c->work_n, nb));
+  CISOR_TRY(call.out(st->s, c->f, nb));
+  CISOR_TRY(call.leave());
+  st->t = tn;
+  st->k += 1;
+  st->D = D;
+  return s1;
+}
+
+cisor_status cisor_launch_count(const cisor_ctx* c, long long* count) {
+  if (!c || !count) {
+    set_error("cisor_launch_count: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  *count = c->launches;
+  return CISOR_OK;
+}
+
+cisor_status cisor_time_matvec(cisor_ctx* c, const void* f, int adjoint, int reps, double* ms_per_pass) {
+  if (!c || !f || reps < 1 || !ms_per_pass) {
+    set_error("cisor_time_matvec: NULL argument or reps < 1");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  ConvOp op{};
+  op.adjoint = adjoint ? 1 : 0;
+  op.mul_f = 1;
+  op.prologue = PRO_COPY;
+  op.src = c->s;
+  op.epilogue = EPI_MATVEC;
+  op.esrc = c->s;
+  op.out = c->tv;
+  op.f = c->f;
+  op.ntx = c->T;
+  CISOR_TRY(conv_pass(c, op));
+  cudaEvent_t e0, e1;
+  CISOR_CUDA(cudaEventCreate(&e0));
+  CISOR_CUDA(cudaEventCreate(&e1));
+  CISOR_CUDA(cudaEventRecord(e0, c->stream));
+  cisor_status st = CISOR_OK;
+  for (int i = 0; i < reps && st == CISOR_OK; ++i) st = conv_pass(c, op);
+  CISOR_CUDA(cudaEventRecord(e1, c->stream));
+  CISOR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CISOR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CISOR_TRY(st);
+  *ms_per_pass = ms / reps;
+  return call.leave();
+}
+
+}  // extern "C"

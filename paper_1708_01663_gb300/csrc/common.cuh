@@ -1,0 +1,178 @@
+// Internal declarations shared by the translation units of libcisor.
+//
+// Device data layout (all row-major, x index fastest):
+//   fields      [T, n, n]   complex64 (float2), transmitter-major
+//   f           [n, n]      complex64
+//   R (scratch) [T, n, P]   complex64: the padded field after the row FFT,
+//               only the n non-zero rows of the P x P padded image are kept
+//   ghat        [P, P]      complex64: spectrum of the circulant embedding of
+//               G (Sec. II, Eq. 3), pre-scaled by 1/P^2 for the two inverse FFTs
+//   H           [M, N]      complex64 (Eq. 2)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/cisor.h"
+
+namespace cisor {
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 c_cjmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 z_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 z_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 z_div(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__host__ __device__ __forceinline__ double2 z_conj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 z_to_c(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// ---------------------------------------------------------------- per-transmitter Krylov scalars
+// scal[t * SC_STRIDE + i], double2 each
+enum {
+  SC_RHO = 0,     // <rhat, r>
+  SC_ALPHA = 1,
+  SC_OMEGA = 2,
+  SC_BETA = 3,
+  SC_NORMS = 4,   // (||b||^2, ||r||^2)
+  SC_REL = 5,     // (recursive rel. residual, true rel. residual)
+  SC_STRIDE = 8
+};
+
+// dot-product slots written by epilogues: partial sums [T][nblk][3] double2
+enum { DOT_SLOTS = 3 };
+// operand codes for epilogue dot products
+enum { OP_NONE = 0, OP_Y = 1, OP_SRC = 2, OP_AUX = 3 };
+
+// Solver status flags per transmitter
+enum { TX_OK = 0, TX_BREAKDOWN = 1, TX_MAXITER = 2 };
+
+}  // namespace cisor
+
+struct cisor_ctx {
+  // geometry
+  int dim, n, P, T, M, complex_f;
+  long long N;
+  double delta, wavelength, eps_b, k, kb;
+  std::vector<double> tx_angles, rx_pos;
+  int device;
+  cudaStream_t stream;  // internal non-blocking stream; ordered against the caller's via events
+  cudaStream_t user_stream;
+  cudaEvent_t ev_a, ev_b;
+  // tables
+  float2* ghat;   // [P^d], scaled by 1/P^d
+  float2* tw;     // [P] exp(-2 pi i m / P)
+  float2* H;      // [M, N]
+  float2* u_in;   // [T, N]
+  // Krylov workspace, [T, N] each
+  float2 *R, *r, *rhat, *p, *v, *s, *tv, *b;
+  float2 *u, *vadj;   // last forward / adjoint solutions (warm starts)
+  int have_u, have_v;
+  float2 *z, *gz;     // H^H w and z + G^H v
+  float2 *f, *fz, *grad, *work_n;  // [N]
+  float2 *Y, *w, *yobs;          // [T, M]
+  float2* sense_part;            // [ksplit, T, M]
+  int ksplit;
+  double* part;    // [T, nblk, DOT_SLOTS] double2
+  int nblk;        // dot partials per transmitter
+  double* scal;    // [T, SC_STRIDE] double2
+  int *active, *iters, *txflag, *n_active;
+  int* h_n_active;  // pinned
+  double* dsum;     // device scalar accumulators [4]
+  double* h_dsum;   // pinned [4]
+  // TV workspace (2 components x N floats each plane)
+  float *tv_z, *tv_r0, *tv_r1, *tv_p;
+  // graphs of a chunk of BiCGSTAB iterations
+  cudaGraphExec_t graph[2];
+  int graph_ntx[2];
+  float2* graph_x[2];
+  double* sparams;  // device [2]: solve tolerance, iteration cap (read by the captured graphs)
+  int graph_chunk;
+  long long launches;       // kernels launched (graph replays add their kernel count)
+  long long graph_kernels[2];
+};
+
+namespace cisor {
+
+// thread-local last error message
+void set_error(const char* fmt, ...);
+cisor_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CISOR_CUDA(call)                                                      \
+  do {                                                                        \
+    cudaError_t e__ = (call);                                                 \
+    if (e__ != cudaSuccess) return cisor::cuda_fail(e__, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CISOR_TRY(call)                        \
+  do {                                         \
+    cisor_status s__ = (call);                 \
+    if (s__ != CISOR_OK) return s__;           \
+  } while (0)
+
+// tables.cu
+cisor_status build_tables(cisor_ctx* c);
+
+// conv.cu: one batched FFT convolution pass on ntx transmitters.
+struct ConvOp {
+  int adjoint;            // 0: G (prologue multiplies by f); 1: G^H (epilogue multiplies by conj f)
+  int mul_f;              // apply the f factor (A / A^H); 0 gives the bare convolution
+  int prologue;           // PRO_*
+  int epilogue;           // EPI_*
+  const float2* src;      // prologue input: the vector convolved (PRO_COPY), or r (PRO_AXPY / PRO_PUPDATE)
+  const float2* esrc;     // epilogue: the x of A x (EPI_MATVEC, EPI_RESID)
+  float2* pvec;           // p (PRO_PUPDATE, read-write)
+  const float2* vvec;     // v (PRO_PUPDATE, PRO_AXPY)
+  float2* svec;           // s written by PRO_AXPY
+  const float2* f;        // [N]
+  const float2* aux;      // epilogue auxiliary vector (rhat, b, z)
+  float2* out;            // epilogue output
+  float2* out2;           // second epilogue output (copy of out), may be null
+  int dot_a[DOT_SLOTS], dot_b[DOT_SLOTS];  // operand codes per dot slot
+  const int* active;      // may be null
+  const double* scal;     // per-transmitter scalars (alpha, beta, omega)
+  double* part;           // dot partials
+  int ntx;
+};
+enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
+// EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);
+// EPI_CONV_ADD: out = conv + aux (aux may be null)
+enum { EPI_MATVEC = 0, EPI_RESID = 1, EPI_CONV_ADD = 2 };
+cisor_status conv_pass(cisor_ctx* c, const ConvOp& op);
+cisor_status conv_init(int P);
+int conv_rows_per_block(int P);
+
+// solver.cu
+cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float2* b, float2* x,
+                         int ntx, double tol, int max_iter, int* iters_max, double* iters_mean,
+                         double* resid_max, int* n_bad);
+
+// sense.cu
+cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Y, int ntx);
+cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, const float2* y, float2* Z, float2* w,
+                            int ntx);
+cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx);
+cisor_status grad_assemble(cisor_ctx* c, const float2* u, const float2* gz, const float2* s, double gamma,
+                           float2* grad, float2* zstep, int ntx);
+
+// tv.cu
+cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,
+                     double lo_im, double hi_im, int complex_f, const float2* f_prev, double beta_mom,
+                     float2* s_out);
+
+}  // namespace cisor

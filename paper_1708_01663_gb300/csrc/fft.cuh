@@ -1,0 +1,163 @@
+// Block-level Stockham FFTs in shared memory.
+//
+// A CTA transforms `nfft` independent sequences of length P (a power of two,
+// 64..512).  Element i of sequence b lives at buf[b * fs + i * es].  Each
+// stage is the Stockham autosort step (Govindaraju et al., "High performance
+// discrete Fourier transforms on graphics processors", SC 2008): work item j
+// of a sequence reads R inputs at stride P/R, multiplies input r by the
+// twiddle w^(r * (j mod Ns)) with w = exp(-2 pi i / (Ns R)), takes a radix-R
+// DFT in registers and writes the outputs at stride Ns starting from
+// (j - j mod Ns) R + j mod Ns.  Stages ping-pong between two buffers and the
+// result comes out in natural order.  Plan: radix-8 stages, then one radix-4
+// or radix-2 stage for the remaining factor.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / P) (built once in FP64);
+// the inverse transform uses conj(tw) and +i in the butterflies (unnormalised).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace cisor {
+
+template <typename C> struct cx;
+template <> struct cx<float2> {
+  typedef float R;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct cx<double2> {
+  typedef double R;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+
+template <typename C> __device__ __forceinline__ C f_add(C a, C b) { return cx<C>::make(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C f_sub(C a, C b) { return cx<C>::make(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C f_mul(C a, C b) {
+  return cx<C>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <bool INV, typename C> __device__ __forceinline__ C f_rot(C a) {
+  return INV ? cx<C>::make(-a.y, a.x) : cx<C>::make(a.y, -a.x);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a0, C& a1) {
+  C t = a0;
+  a0 = f_add(t, a1);
+  a1 = f_sub(t, a1);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = f_add(a0, a2), t1 = f_sub(a0, a2);
+  C t2 = f_add(a1, a3), t3 = f_rot<INV>(f_sub(a1, a3));
+  a0 = f_add(t0, t2);
+  a1 = f_add(t1, t3);
+  a2 = f_sub(t0, t2);
+  a3 = f_sub(t1, t3);
+}
+
+// radix-8 = two radix-4 DFTs (even / odd inputs) joined by w8^k, k = 0..3
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
+  typedef typename cx<C>::R R;
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const R h = (R)0.70710678118654752440;
+  // w8 = (1 -+ i)/sqrt2 ; w8^2 = -+i ; w8^3 = (-1 -+ i)/sqrt2
+  C w1o = INV ? cx<C>::make(h * (o1.x - o1.y), h * (o1.x + o1.y)) : cx<C>::make(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  C w2o = f_rot<INV>(o2);
+  C w3o = INV ? cx<C>::make(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : cx<C>::make(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = f_add(e0, o0);
+  v[4] = f_sub(e0, o0);
+  v[1] = f_add(e1, w1o);
+  v[5] = f_sub(e1, w1o);
+  v[2] = f_add(e2, w2o);
+  v[6] = f_sub(e2, w2o);
+  v[3] = f_add(e3, w3o);
+  v[7] = f_sub(e3, w3o);
+}
+
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft_r(C* v) {
+  if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else dft2<INV>(v[0], v[1]);
+}
+
+// One Stockham stage over all sequences.  FFT_FAST: consecutive threads walk
+// consecutive sequences (column layouts, es > 1); otherwise consecutive
+// work items of one sequence (row layouts, es = 1).
+template <int P, int R, bool INV, bool FFT_FAST, typename C>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ in, C* __restrict__ out, int Ns, int nfft, int fs,
+                                          int es, const C* __restrict__ tw, int tid, int nthr) {
+  constexpr int Q = P / R;
+  const int total = nfft * Q;
+  for (int w = tid; w < total; w += nthr) {
+    int b, j;
+    if (FFT_FAST) {
+      b = w % nfft;
+      j = w / nfft;
+    } else {
+      b = w / Q;
+      j = w % Q;
+    }
+    const C* src = in + b * fs;
+    C* dst = out + b * fs;
+    const int k = j & (Ns - 1);
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * Q) * es];
+    if (Ns > 1) {
+      const int step = P / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C t = tw[r * k * step];
+        if (INV) t.y = -t.y;
+        v[r] = f_mul(v[r], t);
+      }
+    }
+    dft_r<R, INV>(v);
+    const int d = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(d + r * Ns) * es] = v[r];
+  }
+}
+
+template <int P> struct fft_plan {
+  static constexpr int n8 = (P == 64) ? 2 : (P == 128) ? 2 : (P == 256) ? 2 : (P == 512) ? 3 : -1;
+  static constexpr int rem = (P == 64) ? 1 : (P == 128) ? 2 : (P == 256) ? 4 : (P == 512) ? 1 : -1;
+  static_assert(n8 > 0, "unsupported FFT length");
+  static constexpr int stages = n8 + (rem > 1 ? 1 : 0);
+};
+
+// Full transform.  Input in `a`; returns the buffer that holds the result
+// (a or b).  Caller must __syncthreads() after writing `a` and before reading
+// the result.
+template <int P, bool INV, bool FFT_FAST, typename C>
+__device__ __forceinline__ C* block_fft(C* a, C* b, int nfft, int fs, int es, const C* tw, int tid, int nthr) {
+  C* in = a;
+  C* out = b;
+  int Ns = 1;
+#pragma unroll
+  for (int s = 0; s < fft_plan<P>::n8; ++s) {
+    fft_stage<P, 8, INV, FFT_FAST>(in, out, Ns, nfft, fs, es, tw, tid, nthr);
+    __syncthreads();
+    C* t = in;
+    in = out;
+    out = t;
+    Ns *= 8;
+  }
+  if constexpr (fft_plan<P>::rem == 4) {
+    fft_stage<P, 4, INV, FFT_FAST>(in, out, Ns, nfft, fs, es, tw, tid, nthr);
+    __syncthreads();
+    C* t = in;
+    in = out;
+    out = t;
+  } else if constexpr (fft_plan<P>::rem == 2) {
+    fft_stage<P, 2, INV, FFT_FAST>(in, out, Ns, nfft, fs, es, tw, tid, nthr);
+    __syncthreads();
+    C* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+}  // namespace cisor

@@ -1,0 +1,185 @@
+// One-time tables of a geometry, computed in FP64 on the device and stored
+// as complex64: the spectrum of the circulant embedding of G (Sec. II, Eq. 3,
+// made a pointwise product by the FFT, Sec. III-A), the sensing matrix H
+// (Eq. 2), the incident plane waves and the FFT twiddles.
+//
+// Discretisation (readings of points the paper leaves open):
+//  * g(r) = +(j/4) H0^(1)(k_b r) in 2D.  Eq. 1 prints -(j/4); only +j/4
+//    agrees with the 3D kernel's sign and with u = u_in + k^2 int g f u.
+//  * G_ij = k^2 delta^2 g(|r_i - r_j|) (midpoint rule, as the 3D
+//    discretisation of Appendix A writes delta^3 sum g).
+//  * G_ii (g is singular at 0): k^2 times the integral of g over the disk of
+//    the pixel's area, radius a = delta / sqrt(pi):
+//        G_ii = k^2 [ (j pi a / (2 k_b)) H1^(1)(k_b a) - 1 / k_b^2 ].
+// Bessel functions are CUDA's double-precision j0/y0/j1/y1.
+#include <math.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace cisor {
+
+__global__ void twiddle_kernel(float2* tw32, double2* tw64, int P) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= P) return;
+  double s, c;
+  sincospi(-2.0 * (double)m / (double)P, &s, &c);
+  tw32[m] = make_float2((float)c, (float)s);
+  tw64[m] = make_double2(c, s);
+}
+
+__device__ __forceinline__ double2 green2d_scaled(double r, double k, double kb, double delta) {
+  // k^2 delta^2 (j/4) (J0 + j Y0)(kb r)
+  double x = kb * r;
+  double s = k * k * delta * delta * 0.25;
+  return make_double2(-s * y0(x), s * j0(x));
+}
+
+__device__ __forceinline__ double2 self_term2d(double k, double kb, double delta) {
+  const double a = delta * 0.56418958354775628695;  // delta / sqrt(pi)
+  const double x = kb * a;
+  const double c = 3.14159265358979323846 * a / (2.0 * kb);
+  // (j c)(J1 + j Y1) - 1/kb^2
+  return make_double2(k * k * (-c * y1(x) - 1.0 / (kb * kb)), k * k * c * j1(x));
+}
+
+// First column of the P x P circulant embedding: axis index j holds offset
+// j (j < n), j - P (j > P - n), and nothing in between.
+__global__ void green_column_kernel(double2* cbuf, int n, int P, double delta, double k, double kb) {
+  int jx = blockIdx.x * blockDim.x + threadIdx.x;
+  int jy = blockIdx.y;
+  if (jx >= P) return;
+  int mx = jx < n ? jx : jx - P;
+  int my = jy < n ? jy : jy - P;
+  bool used = (jx < n || jx > P - n) && (jy < n || jy > P - n);
+  double2 v = make_double2(0.0, 0.0);
+  if (used) {
+    if (mx == 0 && my == 0) {
+      v = self_term2d(k, kb, delta);
+    } else {
+      double r = delta * sqrt((double)mx * mx + (double)my * my);
+      v = green2d_scaled(r, k, kb, delta);
+    }
+  }
+  cbuf[(size_t)jy * P + jx] = v;
+}
+
+template <int P>
+__global__ void fft64_rows_kernel(double2* data, const double2* tw_g) {
+  extern __shared__ double2 sm64[];
+  double2* tw = sm64;
+  double2* a = tw + P;
+  double2* b = a + P;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  double2* row = data + (size_t)blockIdx.x * P;
+  for (int i = tid; i < P; i += nthr) {
+    tw[i] = tw_g[i];
+    a[i] = row[i];
+  }
+  __syncthreads();
+  double2* res = block_fft<P, false, false>(a, b, 1, P, 1, tw, tid, nthr);
+  for (int i = tid; i < P; i += nthr) row[i] = res[i];
+}
+
+template <int P>
+__global__ void fft64_cols_kernel(double2* data, const double2* tw_g, float2* out32, double scale) {
+  constexpr int W = 2;
+  extern __shared__ double2 sm64[];
+  double2* tw = sm64;
+  double2* a = tw + P;
+  double2* b = a + P * W;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int c0 = blockIdx.x * W;
+  for (int i = tid; i < P; i += nthr) tw[i] = tw_g[i];
+  for (int e = tid; e < P * W; e += nthr) {
+    int i = e / W, w = e % W;
+    a[e] = data[(size_t)i * P + c0 + w];
+  }
+  __syncthreads();
+  double2* res = block_fft<P, false, true>(a, b, W, 1, W, tw, tid, nthr);
+  for (int e = tid; e < P * W; e += nthr) {
+    int i = e / W, w = e % W;
+    double2 v = res[e];
+    out32[(size_t)i * P + c0 + w] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+  }
+}
+
+__global__ void sensing_kernel(float2* H, const double* rx, int M, int n, double delta, double k, double kb) {
+  long long N = (long long)n * n;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  int m = (int)(idx / N);
+  int p = (int)(idx % N);
+  int ix = p % n, iy = p / n;
+  double x = (ix - n / 2.0 + 0.5) * delta, y = (iy - n / 2.0 + 0.5) * delta;
+  double dx = rx[2 * m] - x, dy = rx[2 * m + 1] - y;
+  double2 g = green2d_scaled(sqrt(dx * dx + dy * dy), k, kb, delta);
+  H[idx] = make_float2((float)g.x, (float)g.y);
+}
+
+__global__ void plane_wave_kernel(float2* u, const double* ang, int T, int n, double delta, double kb) {
+  long long N = (long long)n * n;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)T * N) return;
+  int t = (int)(idx / N);
+  int p = (int)(idx % N);
+  int ix = p % n, iy = p / n;
+  double x = (ix - n / 2.0 + 0.5) * delta, y = (iy - n / 2.0 + 0.5) * delta;
+  double s, c, sa, ca;
+  sincos(ang[t], &sa, &ca);
+  sincos(kb * (ca * x + sa * y), &s, &c);
+  u[idx] = make_float2((float)c, (float)s);
+}
+
+template <int P>
+static cisor_status spectrum_fft(cisor_ctx* c, double2* cbuf, const double2* tw64) {
+  size_t sm_rows = 3 * P * sizeof(double2);
+  size_t sm_cols = (P + 2 * P * 2) * sizeof(double2);
+  CISOR_CUDA(cudaFuncSetAttribute(fft64_cols_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cols));
+  fft64_rows_kernel<P><<<P, 128, sm_rows, c->stream>>>(cbuf, tw64);
+  CISOR_CUDA(cudaGetLastError());
+  fft64_cols_kernel<P><<<P / 2, 128, sm_cols, c->stream>>>(cbuf, tw64, c->ghat, 1.0 / ((double)P * P));
+  CISOR_CUDA(cudaGetLastError());
+  return CISOR_OK;
+}
+
+cisor_status build_tables(cisor_ctx* c) {
+  const int P = c->P, n = c->n;
+  double2* cbuf = nullptr;
+  double2* tw64 = nullptr;
+  double* d_rx = nullptr;
+  double* d_ang = nullptr;
+  CISOR_CUDA(cudaMallocAsync((void**)&cbuf, sizeof(double2) * P * P, c->stream));
+  CISOR_CUDA(cudaMallocAsync((void**)&tw64, sizeof(double2) * P, c->stream));
+  CISOR_CUDA(cudaMallocAsync((void**)&d_rx, sizeof(double) * 2 * c->M, c->stream));
+  CISOR_CUDA(cudaMallocAsync((void**)&d_ang, sizeof(double) * c->T, c->stream));
+  CISOR_CUDA(cudaMemcpyAsync(d_rx, c->rx_pos.data(), sizeof(double) * 2 * c->M, cudaMemcpyHostToDevice, c->stream));
+  CISOR_CUDA(cudaMemcpyAsync(d_ang, c->tx_angles.data(), sizeof(double) * c->T, cudaMemcpyHostToDevice, c->stream));
+
+  twiddle_kernel<<<(P + 127) / 128, 128, 0, c->stream>>>(c->tw, tw64, P);
+  CISOR_CUDA(cudaGetLastError());
+  dim3 g1((P + 127) / 128, P);
+  green_column_kernel<<<g1, 128, 0, c->stream>>>(cbuf, n, P, c->delta, c->k, c->kb);
+  CISOR_CUDA(cudaGetLastError());
+  switch (P) {
+    case 64: CISOR_TRY(spectrum_fft<64>(c, cbuf, tw64)); break;
+    case 128: CISOR_TRY(spectrum_fft<128>(c, cbuf, tw64)); break;
+    case 256: CISOR_TRY(spectrum_fft<256>(c, cbuf, tw64)); break;
+    case 512: CISOR_TRY(spectrum_fft<512>(c, cbuf, tw64)); break;
+    default: set_error("unsupported FFT size %d", P); return CISOR_ERR_INVALID_ARG;
+  }
+  long long MN = (long long)c->M * c->N;
+  sensing_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
+  CISOR_CUDA(cudaGetLastError());
+  long long TN = (long long)c->T * c->N;
+  plane_wave_kernel<<<(unsigned)((TN + 255) / 256), 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta, c->kb);
+  CISOR_CUDA(cudaGetLastError());
+  CISOR_CUDA(cudaFreeAsync(cbuf, c->stream));
+  CISOR_CUDA(cudaFreeAsync(tw64, c->stream));
+  CISOR_CUDA(cudaFreeAsync(d_rx, c->stream));
+  CISOR_CUDA(cudaFreeAsync(d_ang, c->stream));
+  CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  return CISOR_OK;
+}
+
+}  // namespace cisor

@@ -1,0 +1,143 @@
+// prox of gamma R, R = tau TV_iso + chi_C (Eq. 8), by the fast gradient
+// projection (FGP) method of Beck and Teboulle (IEEE TIP 2009), which the
+// paper cites for this prox (Sec. III-A) without restating it.  On the dual
+// p = (p_x, p_y), with lam = gamma tau, D the forward difference (zero at the
+// last index) and P_C the box clamp:
+//     x(r)    = P_C(z - lam D^T r)
+//     p_k     = Pi_unit-disk(r_k + D x(r_k) / (8 lam))
+//     t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+//     r_{k+1} = p_k + ((t_k - 1) / t_{k+1}) (p_k - p_{k-1})
+// from r_1 = p_0 = 0, t_1 = 1; output x(p_K).  One kernel per FGP iteration
+// (r ping-pongs between two buffers; p is updated in place per pixel); the
+// right neighbour's x comes from the next lane by warp shuffle.  Complex f
+// takes the separable prox: Re and Im planes, each with its own box.
+// The last kernel also applies the relaxed-FISTA momentum of Eq. 11,
+// s_{k+1} = f_k + beta (f_k - f_{k-1}).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace cisor {
+
+__global__ void tv_split_kernel(const float2* __restrict__ z, float* __restrict__ zp, float* __restrict__ r,
+                                float* __restrict__ p, long long N, int ncomp) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float2 v = z[i];
+  zp[i] = v.x;
+  if (ncomp == 2) zp[N + i] = v.y;
+  for (int c = 0; c < ncomp; ++c) {
+    r[2 * c * N + i] = 0.f;
+    r[(2 * c + 1) * N + i] = 0.f;
+    p[2 * c * N + i] = 0.f;
+    p[(2 * c + 1) * N + i] = 0.f;
+  }
+}
+
+// (D^T r)(iy, ix) for the forward difference with zero difference at the last index
+__device__ __forceinline__ float dt_at(const float* __restrict__ rx, const float* __restrict__ ry, int iy, int ix,
+                                       int n) {
+  const int i = iy * n + ix;
+  float v = 0.f;
+  if (ix < n - 1) v -= rx[i];
+  if (ix > 0) v += rx[i - 1];
+  if (iy < n - 1) v -= ry[i];
+  if (iy > 0) v += ry[i - n];
+  return v;
+}
+
+__global__ void tv_iter_kernel(const float* __restrict__ zp, const float* __restrict__ rin, float* __restrict__ rout,
+                               float* __restrict__ p, int n, float lam, float step, float beta, float lo0, float hi0,
+                               float lo1, float hi1) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y, c = blockIdx.z;
+  const long long N = (long long)n * n;
+  const float lo = c ? lo1 : lo0, hi = c ? hi1 : hi0;
+  const float* z = zp + c * N;
+  const float* rx = rin + 2 * c * N;
+  const float* ry = rx + N;
+  const bool valid = ix < n;
+  const int xi = valid ? ix : n - 1;
+  const int i = iy * n + xi;
+  const float x0 = fminf(fmaxf(z[i] - lam * dt_at(rx, ry, iy, xi, n), lo), hi);
+  // right neighbour from the next lane; the last lane of a warp computes it itself
+  float xr = __shfl_down_sync(0xffffffffu, x0, 1);
+  const int lane = threadIdx.x & 31;
+  if (lane == 31 && xi < n - 1) xr = fminf(fmaxf(z[i + 1] - lam * dt_at(rx, ry, iy, xi + 1, n), lo), hi);
+  if (!valid) return;
+  const float dx = (ix < n - 1) ? xr - x0 : 0.f;
+  float dy = 0.f;
+  if (iy < n - 1) dy = fminf(fmaxf(z[i + n] - lam * dt_at(rx, ry, iy + 1, ix, n), lo), hi) - x0;
+  const float qx = rx[i] + step * dx, qy = ry[i] + step * dy;
+  const float nrm = fmaxf(1.f, sqrtf(qx * qx + qy * qy));
+  const float px = qx / nrm, py = qy / nrm;
+  float* pc = p + 2 * c * N;
+  const float pox = pc[i], poy = pc[N + i];
+  pc[i] = px;
+  pc[N + i] = py;
+  float* ro = rout + 2 * c * N;
+  ro[i] = px + beta * (px - pox);
+  ro[N + i] = py + beta * (py - poy);
+}
+
+__global__ void tv_final_kernel(const float* __restrict__ zp, const float* __restrict__ p, int n, float lam, float lo0,
+                                float hi0, float lo1, float hi1, int ncomp, float2* x, const float2* fprev,
+                                float beta_mom, float2* __restrict__ s_out) {
+  const long long N = (long long)n * n;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int iy = (int)(i / n), ix = (int)(i % n);
+  float xv[2] = {0.f, 0.f};
+  for (int c = 0; c < ncomp; ++c) {
+    const float lo = c ? lo1 : lo0, hi = c ? hi1 : hi0;
+    const float* pc = p + 2 * c * N;
+    const float d = lam > 0.f ? dt_at(pc, pc + N, iy, ix, n) : 0.f;
+    xv[c] = fminf(fmaxf(zp[c * N + i] - lam * d, lo), hi);
+  }
+  const float2 xo = make_float2(xv[0], xv[1]);
+  if (s_out) {
+    const float2 fp = fprev[i];  // read before x (x may alias fprev)
+    s_out[i] = make_float2(xo.x + beta_mom * (xo.x - fp.x), xo.y + beta_mom * (xo.y - fp.y));
+  }
+  x[i] = xo;
+}
+
+cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,
+                     double lo_im, double hi_im, int complex_f, const float2* f_prev, double beta_mom,
+                     float2* s_out) {
+  const int n = c->n;
+  const long long N = c->N;
+  const int ncomp = complex_f ? 2 : 1;
+  const unsigned gN = (unsigned)((N + 255) / 256);
+  tv_split_kernel<<<gN, 256, 0, c->stream>>>(z, c->tv_z, c->tv_r0, c->tv_p, N, ncomp);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  if (lam > 0.0 && iters > 0) {
+    const int bx = ((n + 31) / 32) * 32 > 256 ? 256 : ((n + 31) / 32) * 32;
+    dim3 g((n + bx - 1) / bx, n, ncomp);
+    double t = 1.0;
+    float* rin = c->tv_r0;
+    float* rout = c->tv_r1;
+    const float step = (float)(1.0 / (8.0 * lam));
+    for (int k = 0; k < iters; ++k) {
+      const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      const float beta = (float)((t - 1.0) / tn);
+      tv_iter_kernel<<<g, bx, 0, c->stream>>>(c->tv_z, rin, rout, c->tv_p, n, (float)lam, step, beta, (float)lo,
+                                              (float)hi, (float)lo_im, (float)hi_im);
+      CISOR_CUDA(cudaGetLastError());
+      c->launches += 1;
+      float* tmp = rin;
+      rin = rout;
+      rout = tmp;
+      t = tn;
+    }
+  }
+  const float lam_f = (lam > 0.0 && iters > 0) ? (float)lam : 0.f;
+  tv_final_kernel<<<gN, 256, 0, c->stream>>>(c->tv_z, c->tv_p, n, lam_f, (float)lo, (float)hi, (float)lo_im,
+                                             (float)hi_im, ncomp, x, f_prev, (float)beta_mom, s_out);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  return CISOR_OK;
+}
+
+}  // namespace cisor
