@@ -142,13 +142,13 @@ static void free_ctx(cisor_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int i = 0; i < 2; ++i)
     if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-  void* dev[] = {c->ghat, c->tw, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
+  void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
-                 c->part, c->scal, c->active, c->iters, c->txflag, c->n_active, c->dsum, c->sparams, c->tv_z,
+                 c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
                  c->tv_r0, c->tv_r1, c->tv_p};
   for (void* p : dev)
     if (p) cudaFree(p);
-  if (c->h_n_active) cudaFreeHost(c->h_n_active);
+  if (c->h_active) cudaFreeHost(c->h_active);
   if (c->h_dsum) cudaFreeHost(c->h_dsum);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
@@ -242,6 +242,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   const size_t TM = (size_t)c->T * c->M * sizeof(float2);
   ALLOC(c->ghat, sizeof(float2) * P * P);
   ALLOC(c->tw, sizeof(float2) * P);
+  ALLOC(c->twst, sizeof(float2) * 2 * 512);
   ALLOC(c->H, (size_t)c->M * c->N * sizeof(float2));
   ALLOC(c->u_in, TN);
   ALLOC(c->R, (size_t)c->T * c->n * P * sizeof(float2));
@@ -264,12 +265,11 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->w, TM);
   ALLOC(c->yobs, TM);
   ALLOC(c->sense_part, TM * c->ksplit);
-  ALLOC(c->part, sizeof(double) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk);
+  ALLOC(c->part, sizeof(float) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk);
   ALLOC(c->scal, sizeof(double) * 2 * SC_STRIDE * (size_t)c->T);
   ALLOC(c->active, sizeof(int) * c->T);
   ALLOC(c->iters, sizeof(int) * c->T);
   ALLOC(c->txflag, sizeof(int) * c->T);
-  ALLOC(c->n_active, sizeof(int));
   ALLOC(c->dsum, sizeof(double) * 4);
   ALLOC(c->sparams, sizeof(double) * 2);
   ALLOC(c->tv_z, sizeof(float) * 2 * c->N);
@@ -278,7 +278,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->tv_p, sizeof(float) * 4 * c->N);
 #undef ALLOC
   {
-    cudaError_t e = cudaMallocHost((void**)&c->h_n_active, sizeof(int));
+    cudaError_t e = cudaMallocHost((void**)&c->h_active, sizeof(int) * c->T);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_dsum, sizeof(double) * 4);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__));
   }

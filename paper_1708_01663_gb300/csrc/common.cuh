@@ -54,7 +54,9 @@ enum {
   SC_STRIDE = 8
 };
 
-// dot-product slots written by epilogues: partial sums [T][nblk][3] double2
+// dot-product slots written by epilogues: partial sums [T][nblk][3] float2
+// (FP32 pairwise tree within a CTA; the per-transmitter sum over CTAs is a
+// second FP32 tree; the Krylov scalars built from them are FP64)
 enum { DOT_SLOTS = 3 };
 // operand codes for epilogue dot products
 enum { OP_NONE = 0, OP_Y = 1, OP_SRC = 2, OP_AUX = 3 };
@@ -77,6 +79,7 @@ struct cisor_ctx {
   // tables
   float2* ghat;   // [P^d], scaled by 1/P^d
   float2* tw;     // [P] exp(-2 pi i m / P)
+  float2* twst;   // [2][512] stage twiddle tables of the forward / reversed FFT plans
   float2* H;      // [M, N]
   float2* u_in;   // [T, N]
   // Krylov workspace, [T, N] each
@@ -88,11 +91,11 @@ struct cisor_ctx {
   float2 *Y, *w, *yobs;          // [T, M]
   float2* sense_part;            // [ksplit, T, M]
   int ksplit;
-  double* part;    // [T, nblk, DOT_SLOTS] double2
+  float* part;     // [T, nblk, DOT_SLOTS] float2
   int nblk;        // dot partials per transmitter
   double* scal;    // [T, SC_STRIDE] double2
-  int *active, *iters, *txflag, *n_active;
-  int* h_n_active;  // pinned
+  int *active, *iters, *txflag;
+  int* h_active;    // pinned [T]
   double* dsum;     // device scalar accumulators [4]
   double* h_dsum;   // pinned [4]
   // TV workspace (2 components x N floats each plane)
@@ -146,7 +149,7 @@ struct ConvOp {
   int dot_a[DOT_SLOTS], dot_b[DOT_SLOTS];  // operand codes per dot slot
   const int* active;      // may be null
   const double* scal;     // per-transmitter scalars (alpha, beta, omega)
-  double* part;           // dot partials
+  float* part;            // dot partials [T, nblk, DOT_SLOTS] float2
   int ntx;
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };

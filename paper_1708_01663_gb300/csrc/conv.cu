@@ -19,117 +19,138 @@
 // ghat is pre-scaled by 1/P^2, so the inverse transforms are unnormalised.
 #include "common.cuh"
 #include "fft.cuh"
+#include "regfft.cuh"
 
 namespace cisor {
 
 template <int P> struct ConvCfg {
-  static constexpr int RB = (2048 / P) < 1 ? 1 : 2048 / P;  // rows per CTA, row passes
-  static constexpr int W = 8;                               // columns per CTA, column pass
-  static constexpr int NT = 256;
+  static constexpr int NTF = P / 8;         // threads per P-point transform
+  static constexpr int RB = 256 / NTF;      // rows per CTA, row passes (256 threads)
+  static constexpr int PP = P + P / 16;     // padded row pitch in shared memory
+  static constexpr int W = 512 / NTF;       // columns per CTA, column pass (512 threads)
 };
 
-int conv_rows_per_block(int P) { return (2048 / P) < 1 ? 1 : 2048 / P; }
+int conv_rows_per_block(int P) { return 2048 / P; }
 
 template <int P, int PRO>
 __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const float2* __restrict__ tw_g,
                                                      float2* __restrict__ R, int n) {
-  constexpr int RB = ConvCfg<P>::RB, NT = ConvCfg<P>::NT;
-  __shared__ float2 tw[P];
-  __shared__ float2 bufA[RB * P];
-  __shared__ float2 bufB[RB * P];
-  const int t = blockIdx.y;
-  if (op.active && !op.active[t]) return;
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * RB;
+  typedef ConvCfg<P> C;
+  typedef RPlan<P> PL;
+  __shared__ float2 tw[TwTable<P, false>::SIZE];
+  __shared__ float2 buf[C::RB * C::PP];
+  const int tx = blockIdx.y;
+  if (op.active && !op.active[tx]) return;
+  const int lt = threadIdx.x % C::NTF, row = threadIdx.x / C::NTF;
+  const int iy = blockIdx.x * C::RB + row;
+  const bool rowok = iy < n;
   const long long N = (long long)n * n;
-  for (int i = tid; i < P; i += NT) tw[i] = tw_g[i];
+  for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 256) tw[i] = tw_g[i];
   float2 alpha = make_float2(0.f, 0.f), beta = alpha, omega = alpha;
   if (PRO != PRO_COPY) {
-    const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)t * SC_STRIDE;
+    const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)tx * SC_STRIDE;
     alpha = z_to_c(sc[SC_ALPHA]);
     beta = z_to_c(sc[SC_BETA]);
     omega = z_to_c(sc[SC_OMEGA]);
   }
   const bool mulf = op.mul_f && !op.adjoint;
-  for (int e = tid; e < RB * P; e += NT) {
-    const int row = e / P, ix = e % P;
-    const int iy = row0 + row;
-    float2 q = make_float2(0.f, 0.f);
-    if (ix < n && iy < n) {
-      const long long idx = t * N + (long long)iy * n + ix;
-      if (PRO == PRO_COPY) {
-        q = op.src[idx];
-      } else if (PRO == PRO_PUPDATE) {
-        float2 r = op.src[idx], p = r;
-        if (beta.x != 0.f || beta.y != 0.f) {  // beta = 0 starts (or restarts) with p = r
-          const float2 pold = op.pvec[idx], v = op.vvec[idx];
-          p = c_add(r, c_mul(beta, c_sub(pold, c_mul(omega, v))));
+  const bool fresh = (beta.x == 0.f && beta.y == 0.f);  // beta = 0 starts (or restarts) with p = r
+  constexpr int R0 = PL::template first<false>();
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8 / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int ix = PL::elem(lt, q, r, R0);
+      float2 val = make_float2(0.f, 0.f);
+      if (rowok && ix < n) {
+        const long long pix = (long long)iy * n + ix;
+        const long long idx = tx * N + pix;
+        if (PRO == PRO_COPY) {
+          val = op.src[idx];
+        } else if (PRO == PRO_PUPDATE) {
+          const float2 rv = op.src[idx];
+          float2 p = rv;
+          if (!fresh) p = c_add(rv, c_mul(beta, c_sub(op.pvec[idx], c_mul(omega, op.vvec[idx]))));
+          op.pvec[idx] = p;
+          val = p;
+        } else {  // PRO_AXPY
+          const float2 s = c_sub(op.src[idx], c_mul(alpha, op.vvec[idx]));
+          op.svec[idx] = s;
+          val = s;
         }
-        op.pvec[idx] = p;
-        q = p;
-      } else {  // PRO_AXPY
-        float2 r = op.src[idx], v = op.vvec[idx];
-        float2 s = c_sub(r, c_mul(alpha, v));
-        op.svec[idx] = s;
-        q = s;
+        if (mulf) val = c_mul(val, op.f[pix]);
       }
-      if (mulf) q = c_mul(q, op.f[(long long)iy * n + ix]);
+      v[q * R0 + r] = val;
     }
-    bufA[e] = q;
-  }
-  __syncthreads();
-  const float2* res = block_fft<P, false, false>(bufA, bufB, RB, P, 1, tw, tid, NT);
-  for (int e = tid; e < RB * P; e += NT) {
-    const int row = e / P, ix = e % P;
-    const int iy = row0 + row;
-    if (iy < n) R[((long long)t * n + iy) * P + ix] = res[e];
-  }
+  reg_fft<P, false, false>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
+  if (!rowok) return;
+  constexpr int RL = PL::template last<false>();
+  float2* dst = R + ((long long)tx * n + iy) * P;
+#pragma unroll
+  for (int q = 0; q < 8 / RL; ++q)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) dst[PL::elem(lt, q, r, RL)] = v[q * RL + r];
 }
 
 template <int P, bool ADJ>
-__global__ void __launch_bounds__(256) conv_cols(const int* __restrict__ active, const float2* __restrict__ tw_g,
-                                                 const float2* __restrict__ ghat, float2* __restrict__ R, int n) {
-  constexpr int W = ConvCfg<P>::W, NT = ConvCfg<P>::NT;
-  extern __shared__ float2 smc[];
-  float2* tw = smc;
-  float2* A = tw + P;
-  float2* B = A + P * W;
-  const int t = blockIdx.y;
-  if (active && !active[t]) return;
-  const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * W;
-  for (int i = tid; i < P; i += NT) tw[i] = tw_g[i];
-  float2* base = R + (long long)t * n * P + c0;
-  for (int e = tid; e < P * W; e += NT) {
-    const int i = e / W, w = e % W;
-    A[e] = (i < n) ? base[(long long)i * P + w] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  float2* res = block_fft<P, false, true>(A, B, W, 1, W, tw, tid, NT);
-  float2* other = (res == A) ? B : A;
-  for (int e = tid; e < P * W; e += NT) {
-    const int i = e / W, w = e % W;
-    float2 g = ghat[(long long)i * P + c0 + w];
-    if (ADJ) g.y = -g.y;
-    res[e] = c_mul(res[e], g);
-  }
-  __syncthreads();
-  const float2* res2 = block_fft<P, true, true>(res, other, W, 1, W, tw, tid, NT);
-  for (int e = tid; e < n * W; e += NT) {
-    const int i = e / W, w = e % W;
-    base[(long long)i * P + w] = res2[e];
-  }
+__global__ void __launch_bounds__(512, 2) conv_cols(const int* __restrict__ active, const float2* __restrict__ tw_g,
+                                                    const float2* __restrict__ ghat, float2* __restrict__ R, int n) {
+  typedef ConvCfg<P> C;
+  typedef RPlan<P> PL;
+  __shared__ float2 tw[TwTable<P, false>::SIZE];
+  __shared__ float2 twr[TwTable<P, true>::SIZE];
+  __shared__ float2 buf[P * C::W];
+  const int tx = blockIdx.y;
+  if (active && !active[tx]) return;
+  const int w = threadIdx.x % C::W, lt = threadIdx.x / C::W;
+  const int c0 = blockIdx.x * C::W;
+  for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 512) tw[i] = tw_g[i];
+  for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 512) twr[i] = tw_g[TW_STRIDE + i];
+  float2* base = R + (long long)tx * n * P + c0 + w;
+  constexpr int R0 = PL::template first<false>();
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8 / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int i = PL::elem(lt, q, r, R0);
+      v[q * R0 + r] = (i < n) ? base[(long long)i * P] : make_float2(0.f, 0.f);
+    }
+  const ColLay<C::W> lay{w};
+  reg_fft<P, false, false>(v, buf, lay, lay, lt, tw);
+  // spectrum product in registers: forward outputs are the inverse (reversed plan) inputs
+  constexpr int RL = PL::template last<false>();
+#pragma unroll
+  for (int q = 0; q < 8 / RL; ++q)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int ky = PL::elem(lt, q, r, RL);
+      float2 g = __ldg(ghat + (long long)ky * P + c0 + w);
+      if (ADJ) g.y = -g.y;
+      v[q * RL + r] = c_mul(v[q * RL + r], g);
+    }
+  reg_fft<P, true, true>(v, buf, lay, lay, lt, twr);
+  constexpr int RI = PL::template last<true>();
+#pragma unroll
+  for (int q = 0; q < 8 / RI; ++q)
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+      const int i = PL::elem(lt, q, r, RI);
+      if (i < n) base[(long long)i * P] = v[q * RI + r];
+    }
 }
 
 __device__ __forceinline__ float2 pick(int code, float2 y, float2 s, float2 a) {
   return code == OP_Y ? y : (code == OP_SRC ? s : a);
 }
 
-// Block-wide sum of three complex FP32 partials into FP64, written to part.
+// Block-wide sum of three complex FP32 partials: warp shuffles, then the
+// per-warp sums pairwise in shared memory (all FP32), written to part.
 template <int NT>
-__device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], double2* out) {
-  __shared__ double red[NT / 32][2 * DOT_SLOTS];
-  double v[2 * DOT_SLOTS];
+__device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], float2* out) {
+  __shared__ float red[2 * DOT_SLOTS][NT / 32];
+  float v[2 * DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) {
     v[2 * s] = acc[s].x;
@@ -143,100 +164,109 @@ __device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], double2*
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 2 * DOT_SLOTS; ++k) red[wid][k] = v[k];
+    for (int k = 0; k < 2 * DOT_SLOTS; ++k) red[k][wid] = v[k];
   }
   __syncthreads();
   if (threadIdx.x < 2 * DOT_SLOTS) {
-    double s = 0.0;
+    float* r = red[threadIdx.x];
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-    reinterpret_cast<double*>(out)[threadIdx.x] = s;
+    for (int w = NT / 64; w > 0; w >>= 1)
+#pragma unroll
+      for (int i = 0; i < w; ++i) r[i] += r[i + w];
+    reinterpret_cast<float*>(out)[threadIdx.x] = r[0];
   }
 }
 
 template <int P, int EPI>
 __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const float2* __restrict__ tw_g,
                                                      const float2* __restrict__ R, int n, int nblk) {
-  constexpr int RB = ConvCfg<P>::RB, NT = ConvCfg<P>::NT;
-  __shared__ float2 tw[P];
-  __shared__ float2 bufA[RB * P];
-  __shared__ float2 bufB[RB * P];
-  const int t = blockIdx.y;
-  if (op.active && !op.active[t]) return;
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * RB;
+  typedef ConvCfg<P> C;
+  typedef RPlan<P> PL;
+  __shared__ float2 tw[TwTable<P, true>::SIZE];
+  __shared__ float2 buf[C::RB * C::PP];
+  const int tx = blockIdx.y;
+  if (op.active && !op.active[tx]) return;
+  const int lt = threadIdx.x % C::NTF, row = threadIdx.x / C::NTF;
+  const int iy = blockIdx.x * C::RB + row;
+  const bool rowok = iy < n;
   const long long N = (long long)n * n;
-  for (int i = tid; i < P; i += NT) tw[i] = tw_g[i];
-  for (int e = tid; e < RB * P; e += NT) {
-    const int row = e / P, ix = e % P;
-    const int iy = row0 + row;
-    bufA[e] = (iy < n) ? R[((long long)t * n + iy) * P + ix] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const float2* res = block_fft<P, true, false>(bufA, bufB, RB, P, 1, tw, tid, NT);
+  for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 256) tw[i] = tw_g[TW_STRIDE + i];
+  constexpr int R0 = PL::template first<true>();
+  const float2* srow = R + ((long long)tx * n + (rowok ? iy : 0)) * P;
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8 / R0; ++q)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[q * R0 + r] = rowok ? srow[PL::elem(lt, q, r, R0)] : make_float2(0.f, 0.f);
+  reg_fft<P, true, true>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
   const bool postf = op.mul_f && op.adjoint;
   const bool any_dot = (op.dot_a[0] | op.dot_a[1] | op.dot_a[2]) != 0;
+  const bool aux0 = EPI == EPI_MATVEC && (op.dot_a[0] == OP_AUX || op.dot_b[0] == OP_AUX);
   float2 acc[DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) acc[s] = make_float2(0.f, 0.f);
-  for (int e = tid; e < RB * n; e += NT) {
-    const int row = e / n, ix = e % n;
-    const int iy = row0 + row;
-    if (iy >= n) continue;
-    const long long pix = (long long)iy * n + ix;
-    const long long idx = t * N + pix;
-    float2 c = res[row * P + ix];
-    if (postf) c = c_cjmul(op.f[pix], c);
-    float2 src = make_float2(0.f, 0.f), aux = src, y;
-    if (EPI == EPI_MATVEC) {
-      src = op.esrc[idx];
-      y = c_sub(src, c);
-    } else if (EPI == EPI_RESID) {
-      src = op.esrc[idx];
-      aux = op.aux[idx];
-      y = c_sub(aux, c_sub(src, c));
-    } else {
-      if (op.aux) aux = op.aux[idx];
-      y = c_add(c, aux);
-    }
-    op.out[idx] = y;
-    if (op.out2) op.out2[idx] = y;
-    if (any_dot) {
-      if (EPI == EPI_MATVEC && (op.dot_a[0] == OP_AUX || op.dot_b[0] == OP_AUX)) aux = op.aux[idx];
+  constexpr int RL = PL::template last<true>();
+  if (rowok) {
 #pragma unroll
-      for (int s = 0; s < DOT_SLOTS; ++s) {
-        if (op.dot_a[s]) {
-          float2 a = pick(op.dot_a[s], y, src, aux), b = pick(op.dot_b[s], y, src, aux);
-          acc[s] = c_add(acc[s], c_cjmul(a, b));
+    for (int q = 0; q < 8 / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int ix = PL::elem(lt, q, r, RL);
+        if (ix >= n) continue;
+        const long long pix = (long long)iy * n + ix;
+        const long long idx = tx * N + pix;
+        float2 c = v[q * RL + r];
+        if (postf) c = c_cjmul(op.f[pix], c);
+        float2 src = make_float2(0.f, 0.f), aux = src, y;
+        if (EPI == EPI_MATVEC) {
+          src = op.esrc[idx];
+          y = c_sub(src, c);
+          if (aux0) aux = op.aux[idx];
+        } else if (EPI == EPI_RESID) {
+          src = op.esrc[idx];
+          aux = op.aux[idx];
+          y = c_sub(aux, c_sub(src, c));
+        } else {
+          if (op.aux) aux = op.aux[idx];
+          y = c_add(c, aux);
+        }
+        op.out[idx] = y;
+        if (op.out2) op.out2[idx] = y;
+        if (any_dot) {
+#pragma unroll
+          for (int s = 0; s < DOT_SLOTS; ++s) {
+            if (op.dot_a[s]) {
+              const float2 a = pick(op.dot_a[s], y, src, aux), b = pick(op.dot_b[s], y, src, aux);
+              acc[s] = c_add(acc[s], c_cjmul(a, b));
+            }
+          }
         }
       }
-    }
   }
-  if (any_dot) block_dots<NT>(acc, reinterpret_cast<double2*>(op.part) + ((size_t)t * nblk + blockIdx.x) * DOT_SLOTS);
+  if (any_dot) block_dots<256>(acc, reinterpret_cast<float2*>(op.part) + ((size_t)tx * nblk + blockIdx.x) * DOT_SLOTS);
 }
 
 template <int P>
 static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
-  constexpr int RB = ConvCfg<P>::RB, W = ConvCfg<P>::W, NT = ConvCfg<P>::NT;
+  typedef ConvCfg<P> C;
   const int n = c->n;
-  dim3 grow((n + RB - 1) / RB, op.ntx);
-  dim3 gcol(P / W, op.ntx);
+  dim3 grow((n + C::RB - 1) / C::RB, op.ntx);
+  dim3 gcol(P / C::W, op.ntx);
   switch (op.prologue) {
-    case PRO_COPY: conv_rows_fwd<P, PRO_COPY><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n); break;
-    case PRO_PUPDATE: conv_rows_fwd<P, PRO_PUPDATE><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n); break;
-    default: conv_rows_fwd<P, PRO_AXPY><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n); break;
+    case PRO_COPY: conv_rows_fwd<P, PRO_COPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
+    case PRO_PUPDATE: conv_rows_fwd<P, PRO_PUPDATE><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
+    default: conv_rows_fwd<P, PRO_AXPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
   }
   CISOR_CUDA(cudaGetLastError());
-  const size_t smc = (size_t)(P + 2 * P * W) * sizeof(float2);
   if (op.adjoint)
-    conv_cols<P, true><<<gcol, NT, smc, c->stream>>>(op.active, c->tw, c->ghat, c->R, n);
+    conv_cols<P, true><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
   else
-    conv_cols<P, false><<<gcol, NT, smc, c->stream>>>(op.active, c->tw, c->ghat, c->R, n);
+    conv_cols<P, false><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
   CISOR_CUDA(cudaGetLastError());
   switch (op.epilogue) {
-    case EPI_MATVEC: conv_rows_inv<P, EPI_MATVEC><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n, c->nblk); break;
-    case EPI_RESID: conv_rows_inv<P, EPI_RESID><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n, c->nblk); break;
-    default: conv_rows_inv<P, EPI_CONV_ADD><<<grow, NT, 0, c->stream>>>(op, c->tw, c->R, n, c->nblk); break;
+    case EPI_MATVEC: conv_rows_inv<P, EPI_MATVEC><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n, c->nblk); break;
+    case EPI_RESID: conv_rows_inv<P, EPI_RESID><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n, c->nblk); break;
+    default: conv_rows_inv<P, EPI_CONV_ADD><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n, c->nblk); break;
   }
   CISOR_CUDA(cudaGetLastError());
   c->launches += 3;
@@ -245,10 +275,6 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
 
 template <int P>
 static cisor_status conv_init_t() {
-  constexpr int W = ConvCfg<P>::W;
-  const int smc = (P + 2 * P * W) * (int)sizeof(float2);
-  CISOR_CUDA(cudaFuncSetAttribute(conv_cols<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
-  CISOR_CUDA(cudaFuncSetAttribute(conv_cols<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
   return CISOR_OK;
 }
 

@@ -1,0 +1,128 @@
+// Register-boundary Stockham FFT of length P (64..512) for the complex64 hot path.
+//
+// P/8 threads cooperate on one transform and each owns 8 elements in
+// registers.  Stage s (radix R_s, sub-transform size Ns) runs entirely in
+// registers: work item j = t + q P/8 (q < 8/R_s) holds the R_s inputs
+// j + r P/R_s, multiplies input r by exp(-+2 pi i r (j mod Ns) / (Ns R_s)),
+// and takes a radix-R_s DFT (Stockham autosort, Govindaraju et al., SC 2008).
+// Between stages the outputs go to shared memory at (j - j mod Ns) R_s +
+// j mod Ns + r Ns and the next stage's inputs are gathered back: a P-point
+// transform costs (stages - 1) shared-memory exchanges.  The FIRST stage reads
+// its inputs from registers (the caller loads elements t + q P/8 + r P/R_0
+// straight from global memory) and the LAST stage leaves its outputs in
+// registers (element t + q P/8 + r P/R_L), so the caller writes them without
+// another pass.  Plans: 512 = 8.8.8, 256 = 8.8.4, 128 = 8.8.2, 64 = 8.8; the
+// reversed plan (REV) starts with the last radix, so a forward transform's
+// output registers are exactly the input registers of a REV inverse
+// transform: a pointwise product between the two needs no data movement.
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace cisor {
+
+template <int P> struct RPlan {
+  static constexpr int NTF = P / 8;  // threads per transform
+  static constexpr int NSTAGE = (P == 64) ? 2 : 3;
+  static constexpr int LAST = (P == 512) ? 8 : (P == 256) ? 4 : (P == 128) ? 2 : 8;
+  static_assert(P == 64 || P == 128 || P == 256 || P == 512, "unsupported FFT length");
+  template <bool REV> __host__ __device__ static constexpr int radix(int s) {
+    return NSTAGE == 2 ? 8 : (((REV ? 2 - s : s) == 2) ? LAST : 8);
+  }
+  template <bool REV> __host__ __device__ static constexpr int first() { return radix<REV>(0); }
+  template <bool REV> __host__ __device__ static constexpr int last() { return radix<REV>(NSTAGE - 1); }
+  // element held in register q*R + r at the input (R = first radix) / output (R = last radix)
+  __host__ __device__ static constexpr int elem(int t, int q, int r, int R) { return t + q * NTF + r * (P / R); }
+};
+
+// Shared-memory layouts, chosen so that the 16 threads of a half-warp (which
+// move 8-byte elements) hit 16 distinct bank pairs in every exchange pattern
+// of the plans above (checked by enumeration for P = 64..512):
+//  rows, first exchange : transform b at base b*(P + P/16), one pad slot every 16 elements;
+//  rows, second exchange: same region, bit 3 of the index flipped by bit 6;
+//  columns              : element i of column w at W*(i ^ ((i >> 3) & 1)) + w.
+struct RowLayA {
+  int base;
+  __device__ __forceinline__ int operator()(int i) const { return base + i + (i >> 4); }
+};
+struct RowLayB {
+  int base;
+  __device__ __forceinline__ int operator()(int i) const { return base + (i ^ (((i >> 6) & 1) << 3)); }
+};
+template <int W> struct ColLay {
+  int w;
+  __device__ __forceinline__ int operator()(int i) const { return W * (i ^ ((i >> 3) & 1)) + w; }
+};
+
+// Twiddle table of one plan, stage by stage: stage s (s >= 1, sub-transform
+// size NS_s) holds w_s(r, k) = exp(-2 pi i r k / (NS_s R_s)) at
+// offset_s + (r - 1) NS_s + k, so the threads of a warp, which have
+// consecutive k, read consecutive words (no bank conflicts).
+template <int P, bool REV> struct TwTable {
+  static constexpr int R0 = RPlan<P>::template radix<REV>(0);
+  static constexpr int R1 = RPlan<P>::template radix<REV>(1);
+  static constexpr int R2 = RPlan<P>::NSTAGE == 3 ? RPlan<P>::template radix<REV>(2) : 1;
+  static constexpr int OFF1 = 0;                      // stage 1: NS = R0
+  static constexpr int OFF2 = (R1 - 1) * R0;          // stage 2: NS = R0 R1
+  static constexpr int SIZE = OFF2 + (R2 - 1) * R0 * R1;
+};
+constexpr int TW_STRIDE = 512;  // floats2 reserved per plan table
+
+template <int P, int R, int NS, bool INV>
+__device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __restrict__ tws) {
+  constexpr int NTF = P / 8;
+#pragma unroll
+  for (int q = 0; q < 8 / R; ++q) {
+    if constexpr (NS > 1) {
+      const int j = t + q * NTF;
+      const int k = j & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tws[(r - 1) * NS + k];
+        if (INV) w.y = -w.y;
+        v[q * R + r] = c_mul(v[q * R + r], w);
+      }
+    }
+    dft_r<R, INV>(v + q * R);
+  }
+}
+
+// outputs of a stage (radix RO, size NS) to shared memory, then the inputs of the next stage (radix RI)
+template <int P, int RO, int NS, int RI, class LAY>
+__device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY& lay, int t) {
+  constexpr int NTF = P / 8;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8 / RO; ++q) {
+    const int j = t + q * NTF;
+    const int k = j & (NS - 1);
+    const int base = (j - k) * RO + k;
+#pragma unroll
+    for (int r = 0; r < RO; ++r) buf[lay(base + r * NS)] = v[q * RO + r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8 / RI; ++q) {
+    const int j = t + q * NTF;
+#pragma unroll
+    for (int r = 0; r < RI; ++r) v[q * RI + r] = buf[lay(j + r * (P / RI))];
+  }
+}
+
+// Transform the registers v in place (see the file comment for the element
+// mapping); tws is this plan's stage twiddle table (TwTable<P, REV>); lay0 and
+// lay1 are the shared-memory layouts of the first and second exchange.
+template <int P, bool INV, bool REV, class LAY0, class LAY1>
+__device__ __forceinline__ void reg_fft(float2 (&v)[8], float2* buf, const LAY0& lay0, const LAY1& lay1, int t,
+                                        const float2* __restrict__ tws) {
+  typedef TwTable<P, REV> TT;
+  rstage<P, TT::R0, 1, INV>(v, t, tws);
+  rexchange<P, TT::R0, 1, TT::R1>(v, buf, lay0, t);
+  rstage<P, TT::R1, TT::R0, INV>(v, t, tws + TT::OFF1);
+  if constexpr (RPlan<P>::NSTAGE == 3) {
+    rexchange<P, TT::R1, TT::R0, TT::R2>(v, buf, lay1, t);
+    rstage<P, TT::R2, TT::R0 * TT::R1, INV>(v, t, tws + TT::OFF2);
+  }
+}
+
+}  // namespace cisor

@@ -29,108 +29,116 @@ namespace cisor {
 
 enum { SCM_INIT = 0, SCM_ALPHA = 1, SCM_OMEGA = 2, SCM_RHO = 3, SCM_TRUE = 4 };
 
-__global__ void bicg_scalar_kernel(int mode, int ntx, int nblk, const double* __restrict__ part,
-                                   double* __restrict__ scal, int* __restrict__ active, int* __restrict__ iters,
-                                   int* __restrict__ txflag, int* __restrict__ n_active,
-                                   const double* __restrict__ params) {
-  const int t = threadIdx.x;
-  int act = 0;
-  if (t < ntx) {
-    const double tol = params[0];
-    const int max_iter = (int)params[1];
-    double2 d[DOT_SLOTS];
-    for (int s = 0; s < DOT_SLOTS; ++s) d[s] = make_double2(0.0, 0.0);
-    const double2* pp = reinterpret_cast<const double2*>(part) + (size_t)t * nblk * DOT_SLOTS;
-    for (int b = 0; b < nblk; ++b)
-      for (int s = 0; s < DOT_SLOTS; ++s) d[s] = z_add(d[s], pp[b * DOT_SLOTS + s]);
-    double2* sc = reinterpret_cast<double2*>(scal) + (size_t)t * SC_STRIDE;
-    act = active[t];
-    if (mode == SCM_INIT) {
-      const double bn2 = d[0].x, rn2 = d[2].x;
-      const double rel = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
-      sc[SC_NORMS] = make_double2(bn2, rn2);
+// One 32-thread block per transmitter: the lanes sum the per-CTA partials of
+// the three dot slots (FP32 tree), lane 0 advances that transmitter's
+// recurrence in FP64.  (FP64 arithmetic runs at a small fraction of the FP32
+// rate on this part, so FP64 is kept to these few scalar operations.)
+__global__ void __launch_bounds__(32) bicg_scalar_kernel(int mode, int nblk, const float* __restrict__ part,
+                                                         double* __restrict__ scal, int* __restrict__ active,
+                                                         int* __restrict__ iters, int* __restrict__ txflag,
+                                                         const double* __restrict__ params) {
+  const int t = blockIdx.x, lane = threadIdx.x;
+  float d[2 * DOT_SLOTS];
+#pragma unroll
+  for (int k = 0; k < 2 * DOT_SLOTS; ++k) d[k] = 0.f;
+  const float* pp = part + (size_t)t * nblk * DOT_SLOTS * 2;
+  for (int b = lane; b < nblk; b += 32)
+#pragma unroll
+    for (int k = 0; k < 2 * DOT_SLOTS; ++k) d[k] += pp[b * DOT_SLOTS * 2 + k];
+#pragma unroll
+  for (int k = 0; k < 2 * DOT_SLOTS; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
+  if (lane != 0) return;
+  const double tol = params[0];
+  const int max_iter = (int)params[1];
+  const double2 d0 = make_double2(d[0], d[1]), d1 = make_double2(d[2], d[3]), d2 = make_double2(d[4], d[5]);
+  double2* sc = reinterpret_cast<double2*>(scal) + (size_t)t * SC_STRIDE;
+  int act = active[t];
+  if (mode == SCM_INIT) {
+    const double bn2 = d0.x, rn2 = d2.x;
+    const double rel = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
+    sc[SC_NORMS] = make_double2(bn2, rn2);
+    sc[SC_RHO] = make_double2(rn2, 0.0);
+    sc[SC_ALPHA] = make_double2(1.0, 0.0);
+    sc[SC_OMEGA] = make_double2(1.0, 0.0);
+    sc[SC_BETA] = make_double2(0.0, 0.0);
+    sc[SC_REL] = make_double2(rel, rel);
+    iters[t] = 0;
+    txflag[t] = TX_OK;
+    act = (rel > tol && isfinite(rel)) ? 1 : 0;
+  } else if (mode == SCM_ALPHA) {
+    if (act) {
+      const double m = d0.x * d0.x + d0.y * d0.y;
+      if (!(m > 0.0) || !isfinite(m)) {
+        txflag[t] = TX_BREAKDOWN;
+        act = 0;
+      } else {
+        sc[SC_ALPHA] = z_div(sc[SC_RHO], d0);
+      }
+    }
+  } else if (mode == SCM_OMEGA) {
+    if (act) {
+      const double tt = d2.x;
+      sc[SC_OMEGA] = tt > 0.0 ? make_double2(d1.x / tt, d1.y / tt) : make_double2(0.0, 0.0);
+    }
+  } else if (mode == SCM_RHO) {
+    if (act) {
+      const double rn2 = d2.x;
+      const double bn2 = sc[SC_NORMS].x;
+      const int it = iters[t] + 1;
+      iters[t] = it;
+      const double rel = sqrt(rn2 / bn2);
+      sc[SC_NORMS].y = rn2;
+      sc[SC_REL].x = rel;
+      const double2 om = sc[SC_OMEGA];
+      const double rm = d0.x * d0.x + d0.y * d0.y;
+      const double omm = om.x * om.x + om.y * om.y;
+      if (rel <= tol) {
+        act = 0;
+      } else if (!isfinite(rel)) {
+        txflag[t] = TX_BREAKDOWN;
+        act = 0;
+      } else if (it >= max_iter) {
+        txflag[t] = TX_MAXITER;
+        act = 0;
+      } else if (!(rm > 0.0) || !(omm > 0.0)) {
+        txflag[t] = TX_BREAKDOWN;
+        act = 0;
+      } else {
+        sc[SC_BETA] = z_mul(z_div(d0, sc[SC_RHO]), z_div(sc[SC_ALPHA], om));
+        sc[SC_RHO] = d0;
+      }
+    }
+  } else {  // SCM_TRUE: r = b - A x and rhat = r were just recomputed
+    const double rn2 = d2.x;
+    const double bn2 = sc[SC_NORMS].x;
+    const double rel = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
+    sc[SC_REL].y = rel;
+    act = 0;
+    if (rel > tol && isfinite(rel) && iters[t] < max_iter && txflag[t] != TX_MAXITER) {
+      // restart from the current iterate with a fresh shadow residual
+      sc[SC_NORMS].y = rn2;
       sc[SC_RHO] = make_double2(rn2, 0.0);
       sc[SC_ALPHA] = make_double2(1.0, 0.0);
       sc[SC_OMEGA] = make_double2(1.0, 0.0);
       sc[SC_BETA] = make_double2(0.0, 0.0);
-      sc[SC_REL] = make_double2(rel, rel);
-      iters[t] = 0;
       txflag[t] = TX_OK;
-      act = (rel > tol && isfinite(rel)) ? 1 : 0;
-    } else if (mode == SCM_ALPHA) {
-      if (act) {
-        const double2 den = d[0];
-        const double m = den.x * den.x + den.y * den.y;
-        if (!(m > 0.0) || !isfinite(m)) {
-          txflag[t] = TX_BREAKDOWN;
-          act = 0;
-        } else {
-          sc[SC_ALPHA] = z_div(sc[SC_RHO], den);
-        }
-      }
-    } else if (mode == SCM_OMEGA) {
-      if (act) {
-        const double tt = d[2].x;
-        sc[SC_OMEGA] = tt > 0.0 ? make_double2(d[1].x / tt, d[1].y / tt) : make_double2(0.0, 0.0);
-      }
-    } else if (mode == SCM_RHO) {
-      if (act) {
-        const double2 rho_new = d[0];
-        const double rn2 = d[2].x;
-        const double bn2 = sc[SC_NORMS].x;
-        const int it = iters[t] + 1;
-        iters[t] = it;
-        const double rel = sqrt(rn2 / bn2);
-        sc[SC_NORMS].y = rn2;
-        sc[SC_REL].x = rel;
-        const double2 om = sc[SC_OMEGA];
-        const double rm = rho_new.x * rho_new.x + rho_new.y * rho_new.y;
-        const double omm = om.x * om.x + om.y * om.y;
-        if (rel <= tol) {
-          act = 0;
-        } else if (!isfinite(rel)) {
-          txflag[t] = TX_BREAKDOWN;
-          act = 0;
-        } else if (it >= max_iter) {
-          txflag[t] = TX_MAXITER;
-          act = 0;
-        } else if (!(rm > 0.0) || !(omm > 0.0)) {
-          txflag[t] = TX_BREAKDOWN;
-          act = 0;
-        } else {
-          sc[SC_BETA] = z_mul(z_div(rho_new, sc[SC_RHO]), z_div(sc[SC_ALPHA], om));
-          sc[SC_RHO] = rho_new;
-        }
-      }
-    } else {  // SCM_TRUE: r = b - A x and rhat = r were just recomputed
-      const double rn2 = d[2].x;
-      const double bn2 = sc[SC_NORMS].x;
-      const double rel = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
-      sc[SC_REL].y = rel;
-      act = 0;
-      if (rel > tol && isfinite(rel) && iters[t] < max_iter && txflag[t] != TX_MAXITER) {
-        // restart from the current iterate with a fresh shadow residual
-        sc[SC_NORMS].y = rn2;
-        sc[SC_RHO] = make_double2(rn2, 0.0);
-        sc[SC_ALPHA] = make_double2(1.0, 0.0);
-        sc[SC_OMEGA] = make_double2(1.0, 0.0);
-        sc[SC_BETA] = make_double2(0.0, 0.0);
-        txflag[t] = TX_OK;
-        act = 1;
-      }
+      act = 1;
     }
-    active[t] = act;
   }
-  const int total = __syncthreads_count(act);
-  if (threadIdx.x == 0) *n_active = total;
+  active[t] = act;
 }
 
-// x += alpha p + omega s ; r = s - omega t ; partials <rhat, r> (slot 0), <r, r> (slot 2)
+// x += alpha p + omega s ; r = s - omega t ; partials <rhat, r> (slot 0), <r, r> (slot 2).
+// Each CTA covers the RB rows of one transmitter that a row-pass CTA covers,
+// so its partial lands in the same slot layout; two complex values per
+// 16-byte access when the row length is even.
 __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int RB, int nblk, const int* __restrict__ active,
                                                           const double* __restrict__ scal, float2* __restrict__ x,
                                                           const float2* __restrict__ p, const float2* __restrict__ s,
                                                           const float2* __restrict__ tv, float2* __restrict__ r,
-                                                          const float2* __restrict__ rhat, double* __restrict__ part) {
+                                                          const float2* __restrict__ rhat, float* __restrict__ part) {
   const int t = blockIdx.y;
   if (!active[t]) return;
   const double2* sc = reinterpret_cast<const double2*>(scal) + (size_t)t * SC_STRIDE;
@@ -139,47 +147,69 @@ __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int RB, int nbl
   const int row0 = blockIdx.x * RB;
   const int rows = min(RB, n - row0);
   const long long base = t * N + (long long)row0 * n;
-  float2 a0 = make_float2(0.f, 0.f), a2 = a0;
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const long long i = base + e;
-    const float2 pv = p[i], sv = s[i], tv_ = tv[i];
-    float2 xv = x[i];
-    xv = c_add(xv, c_add(c_mul(alpha, pv), c_mul(omega, sv)));
-    x[i] = xv;
-    const float2 rv = c_sub(sv, c_mul(omega, tv_));
-    r[i] = rv;
-    a0 = c_add(a0, c_cjmul(rhat[i], rv));
-    a2.x += rv.x * rv.x + rv.y * rv.y;
+  const int cnt = rows * n;
+  float2 a0 = make_float2(0.f, 0.f);
+  float a2 = 0.f;
+  auto one = [&](long long i, float2 pv, float2 sv, float2 tv_, float2 xv, float2 rh, float2& xo, float2& ro) {
+    xo = c_add(xv, c_add(c_mul(alpha, pv), c_mul(omega, sv)));
+    ro = c_sub(sv, c_mul(omega, tv_));
+    a0 = c_add(a0, c_cjmul(rh, ro));
+    a2 += ro.x * ro.x + ro.y * ro.y;
+  };
+  if ((n & 1) == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p + base);
+    const float4* s4 = reinterpret_cast<const float4*>(s + base);
+    const float4* t4 = reinterpret_cast<const float4*>(tv + base);
+    const float4* h4 = reinterpret_cast<const float4*>(rhat + base);
+    float4* x4 = reinterpret_cast<float4*>(x + base);
+    float4* r4 = reinterpret_cast<float4*>(r + base);
+    for (int e = threadIdx.x; e < cnt / 2; e += blockDim.x) {
+      const float4 pv = p4[e], sv = s4[e], tq = t4[e], hv = h4[e], xv = x4[e];
+      float2 xo0, ro0, xo1, ro1;
+      one(0, make_float2(pv.x, pv.y), make_float2(sv.x, sv.y), make_float2(tq.x, tq.y), make_float2(xv.x, xv.y),
+          make_float2(hv.x, hv.y), xo0, ro0);
+      one(0, make_float2(pv.z, pv.w), make_float2(sv.z, sv.w), make_float2(tq.z, tq.w), make_float2(xv.z, xv.w),
+          make_float2(hv.z, hv.w), xo1, ro1);
+      x4[e] = make_float4(xo0.x, xo0.y, xo1.x, xo1.y);
+      r4[e] = make_float4(ro0.x, ro0.y, ro1.x, ro1.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const long long i = base + e;
+      float2 xo, ro;
+      one(i, p[i], s[i], tv[i], x[i], rhat[i], xo, ro);
+      x[i] = xo;
+      r[i] = ro;
+    }
   }
-  // block reduction in FP64
-  __shared__ double red[8][4];
-  double v[4] = {a0.x, a0.y, a2.x, 0.0};
+  // block reduction, FP32 tree
+  __shared__ float red[3][8];
+  float v[3] = {a0.x, a0.y, a2};
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)
-    for (int k = 0; k < 3; ++k) red[wid][k] = v[k];
+    for (int k = 0; k < 3; ++k) red[k][wid] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float* rr = red[threadIdx.x];
+    for (int w = 4; w > 0; w >>= 1)
+      for (int i = 0; i < w; ++i) rr[i] += rr[i + w];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      s0 += red[w][0];
-      s1 += red[w][1];
-      s2 += red[w][2];
-    }
-    double2* out = reinterpret_cast<double2*>(part) + ((size_t)t * nblk + blockIdx.x) * DOT_SLOTS;
-    out[0] = make_double2(s0, s1);
-    out[1] = make_double2(0.0, 0.0);
-    out[2] = make_double2(s2, 0.0);
+    float2* out = reinterpret_cast<float2*>(part) + ((size_t)t * nblk + blockIdx.x) * DOT_SLOTS;
+    out[0] = make_float2(red[0][0], red[1][0]);
+    out[1] = make_float2(0.f, 0.f);
+    out[2] = make_float2(red[2][0], 0.f);
   }
 }
 
 static cisor_status scalar_step(cisor_ctx* c, int mode, int ntx) {
-  const int thr = ((ntx + 31) / 32) * 32;
-  bicg_scalar_kernel<<<1, thr, 0, c->stream>>>(mode, ntx, c->nblk, c->part, c->scal, c->active, c->iters,
-                                               c->txflag, c->n_active, c->sparams);
+  bicg_scalar_kernel<<<ntx, 32, 0, c->stream>>>(mode, c->nblk, c->part, c->scal, c->active, c->iters, c->txflag,
+                                               c->sparams);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return CISOR_OK;
@@ -285,10 +315,12 @@ static cisor_status get_graph(cisor_ctx* c, int adjoint, float2* x, int ntx, cud
   return CISOR_OK;
 }
 
-static cisor_status read_active(cisor_ctx* c, int* n_active) {
-  CISOR_CUDA(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+static cisor_status read_active(cisor_ctx* c, int ntx, int* n_active) {
+  CISOR_CUDA(cudaMemcpyAsync(c->h_active, c->active, sizeof(int) * ntx, cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaStreamSynchronize(c->stream));
-  *n_active = *c->h_n_active;
+  int s = 0;
+  for (int t = 0; t < ntx; ++t) s += c->h_active[t];
+  *n_active = s;
   return CISOR_OK;
 }
 
@@ -304,7 +336,7 @@ cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float
   CISOR_TRY(residual_pass(c, adjoint, b, x, ntx));
   CISOR_TRY(scalar_step(c, SCM_INIT, ntx));
   int nact = 0;
-  CISOR_TRY(read_active(c, &nact));
+  CISOR_TRY(read_active(c, ntx, &nact));
   cudaGraphExec_t ge = nullptr;
   int done = 0;
   for (int restart = 0; restart < 6 && nact > 0; ++restart) {
@@ -313,11 +345,11 @@ cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float
       CISOR_CUDA(cudaGraphLaunch(ge, c->stream));
       c->launches += c->graph_kernels[adjoint];
       done += c->graph_chunk;
-      CISOR_TRY(read_active(c, &nact));
+      CISOR_TRY(read_active(c, ntx, &nact));
     }
     CISOR_TRY(residual_pass(c, adjoint, b, x, ntx));
     CISOR_TRY(scalar_step(c, SCM_TRUE, ntx));
-    CISOR_TRY(read_active(c, &nact));
+    CISOR_TRY(read_active(c, ntx, &nact));
   }
   if (nact == 0) {
     // every transmitter ended: refresh the true residuals of those that never iterated

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "regfft.cuh"
 
 namespace cisor {
 
@@ -131,6 +132,37 @@ __global__ void plane_wave_kernel(float2* u, const double* ang, int T, int n, do
   u[idx] = make_float2((float)c, (float)s);
 }
 
+// Stage twiddle tables of the forward plan (slot 0) and the reversed plan (slot 1).
+template <int P, bool REV>
+__global__ void stage_twiddle_kernel(float2* out) {
+  typedef TwTable<P, REV> TT;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= TT::SIZE) return;
+  int ns, R, off;
+  if (e < TT::OFF2 || RPlan<P>::NSTAGE == 2) {
+    ns = TT::R0;
+    R = TT::R1;
+    off = TT::OFF1;
+  } else {
+    ns = TT::R0 * TT::R1;
+    R = TT::R2;
+    off = TT::OFF2;
+  }
+  const int r = (e - off) / ns + 1, k = (e - off) % ns;
+  double s, c;
+  sincospi(-2.0 * (double)r * k / ((double)ns * R), &s, &c);
+  out[e] = make_float2((float)c, (float)s);
+}
+
+template <int P>
+static cisor_status stage_twiddles(cisor_ctx* c) {
+  stage_twiddle_kernel<P, false><<<(TW_STRIDE + 127) / 128, 128, 0, c->stream>>>(c->twst);
+  CISOR_CUDA(cudaGetLastError());
+  stage_twiddle_kernel<P, true><<<(TW_STRIDE + 127) / 128, 128, 0, c->stream>>>(c->twst + TW_STRIDE);
+  CISOR_CUDA(cudaGetLastError());
+  return CISOR_OK;
+}
+
 template <int P>
 static cisor_status spectrum_fft(cisor_ctx* c, double2* cbuf, const double2* tw64) {
   size_t sm_rows = 3 * P * sizeof(double2);
@@ -162,10 +194,10 @@ cisor_status build_tables(cisor_ctx* c) {
   green_column_kernel<<<g1, 128, 0, c->stream>>>(cbuf, n, P, c->delta, c->k, c->kb);
   CISOR_CUDA(cudaGetLastError());
   switch (P) {
-    case 64: CISOR_TRY(spectrum_fft<64>(c, cbuf, tw64)); break;
-    case 128: CISOR_TRY(spectrum_fft<128>(c, cbuf, tw64)); break;
-    case 256: CISOR_TRY(spectrum_fft<256>(c, cbuf, tw64)); break;
-    case 512: CISOR_TRY(spectrum_fft<512>(c, cbuf, tw64)); break;
+    case 64: CISOR_TRY(spectrum_fft<64>(c, cbuf, tw64)); CISOR_TRY(stage_twiddles<64>(c)); break;
+    case 128: CISOR_TRY(spectrum_fft<128>(c, cbuf, tw64)); CISOR_TRY(stage_twiddles<128>(c)); break;
+    case 256: CISOR_TRY(spectrum_fft<256>(c, cbuf, tw64)); CISOR_TRY(stage_twiddles<256>(c)); break;
+    case 512: CISOR_TRY(spectrum_fft<512>(c, cbuf, tw64)); CISOR_TRY(stage_twiddles<512>(c)); break;
     default: set_error("unsupported FFT size %d", P); return CISOR_ERR_INVALID_ARG;
   }
   long long MN = (long long)c->M * c->N;

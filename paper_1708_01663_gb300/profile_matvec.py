@@ -1,0 +1,41 @@
+"""Time (and give a profiler something small to capture) one batched FFT matvec.
+
+    python -m paper_1708_01663_gb300.profile_matvec --config c2 --reps 3
+
+Builds the tables of a named workload (seeded phantom, all transmitters) and
+runs one untimed plus ``reps`` timed passes of y_t = A x_t over every
+transmitter through cisor_time_matvec.  Under ``ncu -k regex:conv -c 3`` the
+captured launches are the three kernels of the untimed pass; only the table
+set-up kernels run before them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--adjoint", action="store_true")
+    args = ap.parse_args()
+    import torch
+
+    from paper_1708_01663_gb300 import build, cisor, synth
+    build.build()
+    cfg, f, angles, rx = synth.make_inputs(args.config)
+    ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles, rx, complex_f=cfg["imag"] != 0.0)
+    fd = torch.from_numpy(np.ascontiguousarray(0.9 * f, dtype=np.complex64)).cuda()
+    ms = ctx.time_matvec(fd, adjoint=args.adjoint, reps=args.reps)
+    N = cfg["n"] ** 2
+    alg = cfg["T"] * 16 * N + 8 * N
+    print(json.dumps({"config": args.config, "T": cfg["T"], "n": cfg["n"], "P": ctx.P, "ms_per_pass": ms,
+                      "alg_bytes": alg, "alg_GBps": alg / ms / 1e6}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
