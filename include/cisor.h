@@ -168,6 +168,26 @@ cisor_status cisor_launch_count(const cisor_ctx* ctx, long long* count);
  * the mean milliseconds of one pass.  f: [N] complex64, as in cisor_apply_A. */
 cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int reps, double* ms_per_pass);
 
+/* y = A x (adjoint = 0) or y = A^H x (adjoint = 1), A = I - G diag(f), for
+ * nvec vectors, WITHOUT allocating device memory and without a context.  The
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc
+ * (code inside a host framework that owns all device allocations, or code
+ * that must not allocate while a CUDA graph is being captured).
+ *   ghat_scaled: device [P, P] complex64, the Green spectrum divided by P*P
+ *                (cisor_green_spectrum's output / (P*P));
+ *   f: device [n*n]; x, y: device [nvec, n*n] complex64; 8 <= n <= 256;
+ *   P a power of two in [64, 512] with P >= 2n - 1; stream: cudaStream_t.
+ * Scratch lives in one file-scope device array of 16 MiB that every GPU
+ * loading the library holds until exit; calls needing more (16 bytes x 512
+ * + 8 x nvec x n x P bytes) return CISOR_ERR_INVALID_ARG with a message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Each call rewrites
+ * every scratch value it reads.  Asynchronous on `stream`. */
+cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const void* x, void* y, int n, int P,
+                                  int nvec, int adjoint, void* stream);
+
 /* Last error message of this thread ("" if none). */
 const char* cisor_last_error(void);
 

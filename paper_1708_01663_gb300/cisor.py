@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
+        "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -133,6 +134,15 @@ def ptr(a, count=None, dtype="complex64"):
     if count is not None and arr.size != count:
         raise ValueError(f"expected {count} elements, got {arr.size}")
     return arr.ctypes.data
+
+
+def apply_A_static(ghat_scaled, f, x, y, n, P, adjoint=False, stream=None):
+    """Allocation-free batched matvec (device tensors only): y = A x or A^H x."""
+    nvec = x.numel() // (n * n)
+    st = load().cisor_apply_A_static(ptr(ghat_scaled, P * P), ptr(f, n * n), ptr(x, nvec * n * n),
+                                     ptr(y, nvec * n * n), int(n), int(P), int(nvec), 1 if adjoint else 0,
+                                     _current_stream() if stream is None else stream)
+    return _check(st)
 
 
 def _current_stream():

@@ -130,6 +130,7 @@ cisor_status cuda_fail(cudaError_t e, const char* what, const char* file, int li
 
 // tables.cu
 cisor_status build_tables(cisor_ctx* c);
+cisor_status make_stage_twiddles(cisor_ctx* c);  // stage twiddles of P into c->twst, on c->stream
 
 // conv.cu: one batched FFT convolution pass on ntx transmitters.
 struct ConvOp {

@@ -163,6 +163,17 @@ static cisor_status stage_twiddles(cisor_ctx* c) {
   return CISOR_OK;
 }
 
+cisor_status make_stage_twiddles(cisor_ctx* c) {
+  switch (c->P) {
+    case 64: return stage_twiddles<64>(c);
+    case 128: return stage_twiddles<128>(c);
+    case 256: return stage_twiddles<256>(c);
+    case 512: return stage_twiddles<512>(c);
+  }
+  set_error("unsupported FFT size %d", c->P);
+  return CISOR_ERR_INVALID_ARG;
+}
+
 template <int P>
 static cisor_status spectrum_fft(cisor_ctx* c, double2* cbuf, const double2* tw64) {
   size_t sm_rows = 3 * P * sizeof(double2);
