@@ -33,6 +33,9 @@ if ROOT not in sys.path:
 
 METRIC = "LS field solves/s at residual 1e-4, learned vs cold start; % of HBM peak"
 UNIT = "solves/s"
+# FP32 arithmetic peak of a GB300 from its unit counts and maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _args():
@@ -161,13 +164,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def conv_sources_hash():
+    """Hash of the sources of the convolution kernels (conv.cu, regfft.cuh, fft.cuh)."""
+    h = hashlib.sha256()
+    for name in ("conv.cu", "regfft.cuh", "fft.cuh"):
+        with open(os.path.join(ROOT, "paper_1708_01663_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_summary():
-    """ncu DRAM bytes per matvec pass from profiles/, valid only for the current conv.cu."""
+    """ncu DRAM bytes per matvec pass from profiles/, valid only while the kernels are unchanged."""
     path = os.path.join(ROOT, "profiles", "conv_matvec_c2.md")
-    src = os.path.join(ROOT, "paper_1708_01663_gb300", "csrc", "conv.cu")
     try:
-        with open(src, "rb") as fh:
-            h = hashlib.sha256(fh.read()).hexdigest()[:16]
         with open(path) as fh:
             text = fh.read()
         vals = {}
@@ -175,7 +184,7 @@ def _traffic_summary():
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-        if vals.get("conv_cu_sha256_16") != h:
+        if vals.get("conv_sources_sha256_16") != conv_sources_hash():
             return None
         return float(vals["dram_bytes_per_pass"])
     except Exception:
@@ -291,12 +300,17 @@ def main():
     h2d = y_h.numel() * 8 + 2 * s0_h.numel() * 8
     d2h = 2 * s0_h.numel() * 8
 
-    # roofline of the dominant kernel chain: one batched FFT matvec over all T transmitters
+    # roofline of the dominant kernel chain: one batched FFT matvec over all T transmitters,
+    # timed with CUDA events on the library's own stream (cisor_time_matvec)
     mv_ms = ctx.time_matvec(s0, adjoint=False, reps=20)
     N = n * n
-    alg_bytes = T * 16 * N + 8 * N
-    achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
-    peak, peak_kind = _peaks()
+    P = ctx.P
+    alg_bytes = T * 16 * N + 8 * N                       # read x, write y per transmitter, f once
+    alg_flops = T * 2 * 5 * P * P * np.log2(P * P)       # forward + inverse P^2 FFT per transmitter (unpruned)
+    achieved_tf = alg_flops / (mv_ms * 1e-3) / 1e12
+    achieved_gbs = alg_bytes / (mv_ms * 1e-3) / 1e9
+    hbm_peak, peak_kind = _peaks()
+    fp32_peak = FP32_PEAK_TFLOPS
     traffic = _traffic_summary()
 
     cpu = None
@@ -322,14 +336,19 @@ def main():
                        "l2": "working set > L2 (Krylov vectors 12 x 32 MB)",
                        "parallelism": "independent replicas" if ws > 1 else "single GPU",
                        "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
+                       "fwd_iters_max": max(i["iters_max"] for i in step_infos) if step_infos else None,
+                       "adj_iters_max": max(i["adj_iters_max"] for i in step_infos) if step_infos else None,
                        "adj_iters_mean": float(np.mean(it_a)) if it_a else None,
                        "resid_max": max(i["resid_max"] for i in step_infos) if step_infos else None,
                        "not_converged": sum(i["n_not_converged"] for i in step_infos)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tf / fp32_peak, "traffic": traffic,
                          "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)",
-                         "ms_per_launch": mv_ms, "alg_bytes_per_launch": alg_bytes,
-                         "peak_kind": f"{peak_kind} (copy bandwidth)"},
+                         "ms_per_launch": mv_ms, "alg_flops_per_launch": alg_flops,
+                         "alg_bytes_per_launch": alg_bytes,
+                         "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                         "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth"}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
