@@ -145,6 +145,20 @@ cisor_status cisor_sense_adjoint(cisor_ctx* ctx, const void* f, const void* w, v
 cisor_status cisor_grad(cisor_ctx* ctx, const void* f, const void* y, void* grad_out, double* D_out,
                         const cisor_solve_opts* opts, cisor_solve_info* info);
 
+/* Forward half of cisor_grad, for reverse-mode use: solves A u_t = u_in,t
+ * (Eq. 13), forms w_t = H diag(u_t) f - y_t and D (Eq. 7), and keeps u_t and
+ * w_t in the context (the fields are the checkpoint the backward half
+ * needs; [T, N] complex64 each).  D_out: host double (may be NULL). */
+cisor_status cisor_data_term(cisor_ctx* ctx, const void* f, const void* y, double* D_out,
+                             const cisor_solve_opts* opts, cisor_solve_info* info);
+
+/* Backward half of cisor_grad (Prop. 1): from the u_t, w_t of the last
+ * cisor_data_term on this context, solves A^H v_t = diag(f)^H H^H w_t and
+ * writes g = sum_t conj(u_t) (H^H w_t + G^H v_t) to grad_out ([N] complex64).
+ * CISOR_ERR_INVALID_ARG if no cisor_data_term preceded it. */
+cisor_status cisor_data_backward(cisor_ctx* ctx, void* grad_out, const cisor_solve_opts* opts,
+                                 cisor_solve_info* info);
+
 /* x = argmin_{x in C} 1/2 ||x - z||^2 + gamma_tau TV_iso(x) (prox of Eq. 8)
  * by `iters` FGP iterations (Beck-Teboulle, cited in Sec. III-A), dual cold
  * start; C is the box [lo, hi] for Re and, for complex_f, [lo_im, hi_im] for
@@ -187,6 +201,41 @@ cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int r
  * every scratch value it reads.  Asynchronous on `stream`. */
 cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const void* x, void* y, int n, int P,
                                   int nvec, int adjoint, void* stream);
+
+/* Autotuner of the FFT convolution's tile shape: times the column-FFT kernel
+ * with 512- and 256-thread CTAs (8 or 4 columns per CTA at P = 512) on this
+ * context's sizes, `reps` batched matvecs each with CUDA events, and keeps
+ * the faster.  *cols_nt_out (may be NULL) receives the chosen CTA size.
+ * Results do not depend on the choice. */
+cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
+
+/* ---- Several problems of uneven size, solved together ----
+ * A batch owns one context per geometry (grid side, transmitters and
+ * receivers may all differ).  Its field solves advance every problem in ONE
+ * CUDA-graph launch per chunk of BiCGSTAB iterations (fork to the problems'
+ * streams, join back); the problems' other steps run concurrently on their
+ * own streams.  Arrays are given per problem (arrays of pointers, host or
+ * device).  x0_mode 0 (cold) or 2 (previous solution) only. */
+typedef struct cisor_batch cisor_batch;
+
+/* Create contexts for nprob geometries (1..256); autotune != 0 runs
+ * cisor_autotune on each. */
+cisor_status cisor_batch_create(cisor_batch** out, const cisor_geometry* geoms, int nprob, void* stream,
+                                int autotune);
+cisor_status cisor_batch_destroy(cisor_batch* b);
+
+/* The context of problem i (for table read-back or single-problem calls). */
+cisor_status cisor_batch_context(cisor_batch* b, int i, cisor_ctx** ctx);
+
+/* Forward solves of every problem (Eq. 13): f[i] [N_i], u_out[i] [T_i, N_i]
+ * (u_out or any entry may be NULL); info: array of nprob (may be NULL). */
+cisor_status cisor_batch_forward(cisor_batch* b, const void* const* f, void* const* u_out,
+                                 const cisor_solve_opts* opts, cisor_solve_info* info);
+
+/* D and gradient of every problem (Eq. 7, Prop. 1): y[i] [T_i, M_i],
+ * grad_out[i] [N_i]; D_out: host array of nprob (may be NULL). */
+cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* const* y, void* const* grad_out,
+                              double* D_out, const cisor_solve_opts* opts, cisor_solve_info* info);
 
 /* Last error message of this thread ("" if none). */
 const char* cisor_last_error(void);

@@ -91,6 +91,15 @@ def load(path: str = LIB_PATH):
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
+        "cisor_data_term": [vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_autotune": [vp, i, POINTER(c_int)],
+        "cisor_batch_create": [POINTER(c_void_p), POINTER(Geometry), i, vp, i],
+        "cisor_batch_destroy": [vp],
+        "cisor_batch_context": [vp, i, POINTER(c_void_p)],
+        "cisor_batch_forward": [vp, POINTER(c_void_p), POINTER(c_void_p), POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_batch_grad": [vp, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p), POINTER(c_double),
+                             POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_data_backward": [vp, vp, POINTER(SolveOpts), POINTER(SolveInfo)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -158,10 +167,17 @@ def _current_stream():
 class Cisor:
     """One imaging geometry: tables and workspace on the current CUDA device."""
 
-    def __init__(self, n, delta, tx_angles, rx_pos, wavelength=1.0, eps_b=1.0, complex_f=False, pad=0,
-                 stream=None):
+    def __init__(self, n=None, delta=None, tx_angles=None, rx_pos=None, wavelength=1.0, eps_b=1.0, complex_f=False,
+                 pad=0, stream=None, _handle=None):
         lib = load()
         self._lib = lib
+        self._owned = _handle is None
+        if _handle is not None:  # view of a context owned by a Batch
+            self._ctx = _handle
+            self.stream = stream
+            self.complex_f = bool(complex_f)
+            self._read_sizes()
+            return
         self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64)
         self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, 2)
         g = Geometry(2, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
@@ -170,14 +186,22 @@ class Cisor:
         self._ctx = c_void_p()
         self.stream = _current_stream() if stream is None else stream
         _check(lib.cisor_create(ctypes.byref(self._ctx), ctypes.byref(g), self.stream))
-        n_, P, T, M, N = c_int(), c_int(), c_int(), c_int(), c_longlong()
-        _check(lib.cisor_sizes(self._ctx, ctypes.byref(n_), ctypes.byref(P), ctypes.byref(T), ctypes.byref(M),
-                               ctypes.byref(N)))
-        self.n, self.P, self.T, self.M, self.N = n_.value, P.value, T.value, M.value, N.value
+        self._read_sizes()
         self.complex_f = bool(complex_f)
 
+    def _read_sizes(self):
+        n_, P, T, M, N = c_int(), c_int(), c_int(), c_int(), c_longlong()
+        _check(self._lib.cisor_sizes(self._ctx, ctypes.byref(n_), ctypes.byref(P), ctypes.byref(T),
+                                     ctypes.byref(M), ctypes.byref(N)))
+        self.n, self.P, self.T, self.M, self.N = n_.value, P.value, T.value, M.value, N.value
+
+    def autotune(self, reps=5):
+        nt = c_int()
+        _check(self._lib.cisor_autotune(self._ctx, int(reps), ctypes.byref(nt)))
+        return nt.value
+
     def close(self):
-        if getattr(self, "_ctx", None):
+        if getattr(self, "_ctx", None) and getattr(self, "_owned", True):
             self._lib.cisor_destroy(self._ctx)
             self._ctx = None
 
@@ -231,6 +255,24 @@ class Cisor:
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return D.value, st, info
 
+    def data_term(self, f, y, tol=1e-4, max_iter=2000, x0_mode=0, check=True):
+        """Forward half of grad: D, with the fields kept in the context for data_backward."""
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        info = SolveInfo()
+        D = c_double()
+        st = self._lib.cisor_data_term(self._ctx, ptr(f, self.N), ptr(y, self.T * self.M), ctypes.byref(D),
+                                       ctypes.byref(opts), ctypes.byref(info))
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return D.value, st, info
+
+    def data_backward(self, grad_out, tol=1e-4, max_iter=2000, x0_mode=0, check=True):
+        """Backward half of grad: adjoint solve and gradient assembly (after data_term)."""
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        info = SolveInfo()
+        st = self._lib.cisor_data_backward(self._ctx, ptr(grad_out, self.N), ctypes.byref(opts), ctypes.byref(info))
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return st, info
+
     def tv_prox(self, z, x, gamma_tau, iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5):
         return _check(self._lib.cisor_tv_prox(self._ctx, ptr(z, self.N), ptr(x, self.N), float(gamma_tau),
                                               int(iters), float(lo), float(hi), float(lo_im), float(hi_im)))
@@ -260,3 +302,66 @@ class Cisor:
                                   ctypes.byref(info))
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return st, info
+
+
+def _geometry(g, keep):
+    ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64)
+    rx = np.ascontiguousarray(g["rx_pos"], dtype=np.float64).reshape(-1, 2)
+    keep += [ang, rx]
+    return Geometry(2, int(g["n"]), float(g["delta"]), float(g.get("wavelength", 1.0)), float(g.get("eps_b", 1.0)),
+                    len(ang), ang.ctypes.data_as(POINTER(c_double)), len(rx), rx.ctypes.data_as(POINTER(c_double)),
+                    1 if g.get("complex_f") else 0, int(g.get("pad", 0)))
+
+
+class Batch:
+    """Problems of uneven size solved together (cisor_batch_*): geoms is a list of dicts
+    with n, delta, tx_angles, rx_pos and optionally wavelength, eps_b, complex_f, pad."""
+
+    def __init__(self, geoms, autotune=True, stream=None):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        arr = (Geometry * len(geoms))(*[_geometry(g, self._keep) for g in geoms])
+        self._b = c_void_p()
+        self.stream = _current_stream() if stream is None else stream
+        _check(lib.cisor_batch_create(ctypes.byref(self._b), arr, len(geoms), self.stream, 1 if autotune else 0))
+        self.problems = []
+        for i, g in enumerate(geoms):
+            h = c_void_p()
+            _check(lib.cisor_batch_context(self._b, i, ctypes.byref(h)))
+            self.problems.append(Cisor(_handle=h, stream=self.stream, complex_f=g.get("complex_f", False)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.cisor_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, arrs, counts):
+        return (c_void_p * len(arrs))(*[ptr(a, c) if a is not None else None for a, c in zip(arrs, counts)])
+
+    def forward(self, f, u_out=None, tol=1e-4, max_iter=2000, x0_mode=0, check=True):
+        ps = self.problems
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        infos = (SolveInfo * len(ps))()
+        fp = self._ptrs(f, [p.N for p in ps])
+        up = self._ptrs(u_out, [p.T * p.N for p in ps]) if u_out is not None else None
+        st = self._lib.cisor_batch_forward(self._b, fp, up, ctypes.byref(opts), infos)
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return st, list(infos)
+
+    def grad(self, f, y, grad_out, tol=1e-4, max_iter=2000, x0_mode=0, check=True):
+        ps = self.problems
+        opts = SolveOpts(tol, max_iter, x0_mode)
+        infos = (SolveInfo * len(ps))()
+        D = (c_double * len(ps))()
+        st = self._lib.cisor_batch_grad(self._b, self._ptrs(f, [p.N for p in ps]),
+                                        self._ptrs(y, [p.T * p.M for p in ps]),
+                                        self._ptrs(grad_out, [p.N for p in ps]), D, ctypes.byref(opts), infos)
+        _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return list(D), st, list(infos)

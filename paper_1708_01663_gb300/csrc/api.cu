@@ -96,28 +96,41 @@ static bool solve_ok(cisor_status s) {
   return s == CISOR_OK || s == CISOR_ERR_NOT_CONVERGED || s == CISOR_ERR_BREAKDOWN;
 }
 
-// Gradient machinery on c->f (the point) and c->yobs (the data): forward
-// solve into c->u, w and D, adjoint RHS, adjoint solve into c->vadj,
-// gz = z + G^H v, g = sum_t conj(u_t) gz_t into c->grad and, when zstep is
-// given, zstep = s - gamma g.
-static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s, float2* zstep,
-                              double* D, cisor_solve_info* info) {
+// Forward half of the gradient machinery on c->f (the point) and c->yobs
+// (the data): forward solve into c->u (kept: the fields are the checkpoint the
+// backward half needs), Z, w = Z - y and D.
+static cisor_status data_core(cisor_ctx* c, const cisor_solve_opts* o, double* D, cisor_solve_info* li) {
   const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
   if (o->x0_mode != 2 || !c->have_u) CISOR_CUDA(cudaMemcpyAsync(c->u, c->u_in, vb, cudaMemcpyDeviceToDevice, c->stream));
-  cisor_solve_info li{};
-  int nb1 = 0, nb2 = 0;
-  cisor_status s1 = solve_batch(c, 0, c->f, c->u_in, c->u, c->T, o->tol, o->max_iter, &li.iters_max, &li.iters_mean,
-                                &li.resid_max, &nb1);
+  int nb1 = 0;
+  c->have_w = 0;
+  cisor_status s1 = solve_batch(c, 0, c->f, c->u_in, c->u, c->T, o->tol, o->max_iter, &li->iters_max, &li->iters_mean,
+                                &li->resid_max, &nb1);
   if (!solve_ok(s1)) return s1;
   c->have_u = 1;
+  li->n_not_converged = nb1;
   CISOR_TRY(residual_and_D(c, c->f, c->u, c->yobs, c->Y, c->w, c->T));
+  CISOR_CUDA(cudaMemcpyAsync(c->h_dsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  if (D) *D = c->h_dsum[0];
+  c->have_w = 1;
+  return s1;
+}
+
+// Backward half: adjoint RHS, adjoint solve into c->vadj, gz = z + G^H v,
+// g = sum_t conj(u_t) gz_t into c->grad and, when zstep is given,
+// zstep = s - gamma g.  Needs data_core's u and w.
+static cisor_status adjoint_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s,
+                                 float2* zstep, cisor_solve_info* li) {
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
   CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
   if (o->x0_mode != 2 || !c->have_v) CISOR_CUDA(cudaMemsetAsync(c->vadj, 0, vb, c->stream));
-  cisor_status s2 = solve_batch(c, 1, c->f, c->b, c->vadj, c->T, o->tol, o->max_iter, &li.adj_iters_max,
-                                &li.adj_iters_mean, &li.adj_resid_max, &nb2);
+  int nb2 = 0;
+  cisor_status s2 = solve_batch(c, 1, c->f, c->b, c->vadj, c->T, o->tol, o->max_iter, &li->adj_iters_max,
+                                &li->adj_iters_mean, &li->adj_resid_max, &nb2);
   if (!solve_ok(s2)) return s2;
   c->have_v = 1;
-  li.n_not_converged = nb1 + nb2;
+  li->n_not_converged += nb2;
   ConvOp op{};
   op.adjoint = 1;
   op.mul_f = 0;
@@ -130,9 +143,16 @@ static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double ga
   op.ntx = c->T;
   CISOR_TRY(conv_pass(c, op));
   CISOR_TRY(grad_assemble(c, c->u, c->gz, s, gamma, c->grad, zstep, c->T));
-  CISOR_CUDA(cudaMemcpyAsync(c->h_dsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CISOR_CUDA(cudaStreamSynchronize(c->stream));
-  if (D) *D = c->h_dsum[0];
+  return s2;
+}
+
+static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s, float2* zstep,
+                              double* D, cisor_solve_info* info) {
+  cisor_solve_info li{};
+  cisor_status s1 = data_core(c, o, D, &li);
+  if (!solve_ok(s1)) return s1;
+  cisor_status s2 = adjoint_core(c, o, gamma, s, zstep, &li);
+  if (!solve_ok(s2)) return s2;
   if (info) *info = li;
   return worse(s1, s2);
 }
@@ -212,6 +232,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->rx_pos.assign(g->rx_pos, g->rx_pos + 2 * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
+  c->cols_nt = 512;
   const int RB = conv_rows_per_block(P);
   c->nblk = (c->n + RB - 1) / RB;
   {
@@ -462,6 +483,53 @@ cisor_status cisor_grad(cisor_ctx* c, const void* f, const void* y, void* grad_o
   return st;
 }
 
+cisor_status cisor_data_term(cisor_ctx* c, const void* f, const void* y, double* D_out, const cisor_solve_opts* o,
+                             cisor_solve_info* info) {
+  if (!c || !f || !y) {
+    set_error("cisor_data_term: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
+  double D = 0.0;
+  cisor_solve_info li{};
+  cisor_status st = data_core(c, o, &D, &li);
+  if (!solve_ok(st)) return st;
+  if (D_out) *D_out = D;
+  if (info) *info = li;
+  CISOR_TRY(call.leave());
+  return st;
+}
+
+cisor_status cisor_data_backward(cisor_ctx* c, void* grad_out, const cisor_solve_opts* o, cisor_solve_info* info) {
+  if (!c || !grad_out) {
+    set_error("cisor_data_backward: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
+  if (!c->have_w) {
+    set_error("cisor_data_backward: no preceding cisor_data_term on this context");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  cisor_solve_info li{};
+  cisor_status st = adjoint_core(c, o, 0.0, nullptr, nullptr, &li);
+  if (!solve_ok(st)) return st;
+  CISOR_TRY(call.out(grad_out, c->grad, sizeof(float2) * c->N));
+  if (info) {
+    info->adj_iters_max = li.adj_iters_max;
+    info->adj_iters_mean = li.adj_iters_mean;
+    info->adj_resid_max = li.adj_resid_max;
+    info->n_not_converged = li.n_not_converged;
+  }
+  CISOR_TRY(call.leave());
+  return st;
+}
+
 cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo, double hi,
                            double lo_im, double hi_im) {
   if (!c || !z || !x || iters < 0 || !(lo <= hi) || (c && c->complex_f && !(lo_im <= hi_im))) {
@@ -510,6 +578,58 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
   st->k += 1;
   st->D = D;
   return s1;
+}
+
+cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
+  if (!c || reps < 1) {
+    set_error("cisor_autotune: NULL context or reps < 1");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  CISOR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(float2) * c->N, c->stream));
+  ConvOp op{};
+  op.mul_f = 1;
+  op.prologue = PRO_COPY;
+  op.src = c->s;
+  op.epilogue = EPI_MATVEC;
+  op.esrc = c->s;
+  op.out = c->tv;
+  op.f = c->f;
+  op.ntx = c->T;
+  cudaEvent_t e0, e1;
+  CISOR_CUDA(cudaEventCreate(&e0));
+  CISOR_CUDA(cudaEventCreate(&e1));
+  const int variants[2] = {512, 256};
+  int best = 512;
+  float best_ms = 1e30f;
+  cisor_status st = CISOR_OK;
+  for (int v = 0; v < 2 && st == CISOR_OK; ++v) {
+    c->cols_nt = variants[v];
+    st = conv_pass(c, op);  // warm-up
+    CISOR_CUDA(cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < reps && st == CISOR_OK; ++i) st = conv_pass(c, op);
+    CISOR_CUDA(cudaEventRecord(e1, c->stream));
+    CISOR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CISOR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = variants[v];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CISOR_TRY(st);
+  c->cols_nt = best;
+  for (int i = 0; i < 2; ++i)  // captured graphs hold the previous kernel variant
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+  if (cols_nt_out) *cols_nt_out = best;
+  return call.leave();
 }
 
 cisor_status cisor_launch_count(const cisor_ctx* c, long long* count) {

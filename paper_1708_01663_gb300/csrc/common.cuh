@@ -85,7 +85,7 @@ struct cisor_ctx {
   // Krylov workspace, [T, N] each
   float2 *R, *r, *rhat, *p, *v, *s, *tv, *b;
   float2 *u, *vadj;   // last forward / adjoint solutions (warm starts)
-  int have_u, have_v;
+  int have_u, have_v, have_w;  // warm starts held; data_core's u and w held for the backward half
   float2 *z, *gz;     // H^H w and z + G^H v
   float2 *f, *fz, *grad, *work_n;  // [N]
   float2 *Y, *w, *yobs;          // [T, M]
@@ -107,6 +107,7 @@ struct cisor_ctx {
   double* sparams;  // device [2]: solve tolerance, iteration cap (read by the captured graphs)
   int graph_chunk;
   long long launches;       // kernels launched (graph replays add their kernel count)
+  int cols_nt;              // threads per CTA of the column-FFT kernel (512 or 256), set by the autotuner
   long long graph_kernels[2];
 };
 
@@ -165,6 +166,22 @@ int conv_rows_per_block(int P);
 cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float2* b, float2* x,
                          int ntx, double tol, int max_iter, int* iters_max, double* iters_mean,
                          double* resid_max, int* n_bad);
+
+struct SolveStat {
+  int iters_max, n_bad;
+  double iters_mean, resid_max;
+  cisor_status status;
+};
+// Graph cache and streams of a multi-problem solve (owned by a cisor_batch).
+struct MultiSolve {
+  cudaStream_t main;
+  cudaEvent_t fork;
+  cudaEvent_t* join;            // [np]
+  cudaGraphExec_t graph[2];     // forward / adjoint chunk graphs
+  long long* kernels[2];        // [np] kernels per problem in one replay
+};
+cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2* const* b, double tol, int max_iter,
+                         MultiSolve& ms, SolveStat* st);
 
 // sense.cu
 cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Y, int ntx);

@@ -27,7 +27,7 @@ template <int P> struct ConvCfg {
   static constexpr int NTF = P / 8;         // threads per P-point transform
   static constexpr int RB = 256 / NTF;      // rows per CTA, row passes (256 threads)
   static constexpr int PP = P + P / 16;     // padded row pitch in shared memory
-  static constexpr int W = 512 / NTF;       // columns per CTA, column pass (512 threads)
+  template <int NT> struct Col { static constexpr int W = NT / NTF; };  // columns per CTA, column pass
 };
 
 int conv_rows_per_block(int P) { return 2048 / P; }
@@ -93,20 +93,21 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
     for (int r = 0; r < RL; ++r) dst[PL::elem(lt, q, r, RL)] = v[q * RL + r];
 }
 
-template <int P, bool ADJ>
-__global__ void __launch_bounds__(512, 2) conv_cols(const int* __restrict__ active, const float2* __restrict__ tw_g,
+template <int P, bool ADJ, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict__ active, const float2* __restrict__ tw_g,
                                                     const float2* __restrict__ ghat, float2* __restrict__ R, int n) {
   typedef ConvCfg<P> C;
   typedef RPlan<P> PL;
   __shared__ float2 tw[TwTable<P, false>::SIZE];
   __shared__ float2 twr[TwTable<P, true>::SIZE];
-  __shared__ float2 buf[P * C::W];
+  constexpr int W = C::template Col<NT>::W;
+  __shared__ float2 buf[P * W];
   const int tx = blockIdx.y;
   if (active && !active[tx]) return;
-  const int w = threadIdx.x % C::W, lt = threadIdx.x / C::W;
-  const int c0 = blockIdx.x * C::W;
-  for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 512) tw[i] = tw_g[i];
-  for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 512) twr[i] = tw_g[TW_STRIDE + i];
+  const int w = threadIdx.x % W, lt = threadIdx.x / W;
+  const int c0 = blockIdx.x * W;
+  for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += NT) tw[i] = tw_g[i];
+  for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += NT) twr[i] = tw_g[TW_STRIDE + i];
   float2* base = R + (long long)tx * n * P + c0 + w;
   constexpr int R0 = PL::template first<false>();
   float2 v[8];
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(512, 2) conv_cols(const int* __restrict__ acti
       const int i = PL::elem(lt, q, r, R0);
       v[q * R0 + r] = (i < n) ? base[(long long)i * P] : make_float2(0.f, 0.f);
     }
-  const ColLay<C::W> lay{w};
+  const ColLay<W> lay{w};
   reg_fft<P, false, false>(v, buf, lay, lay, lt, tw);
   // spectrum product in registers: forward outputs are the inverse (reversed plan) inputs
   constexpr int RL = PL::template last<false>();
@@ -251,17 +252,25 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
   typedef ConvCfg<P> C;
   const int n = c->n;
   dim3 grow((n + C::RB - 1) / C::RB, op.ntx);
-  dim3 gcol(P / C::W, op.ntx);
   switch (op.prologue) {
     case PRO_COPY: conv_rows_fwd<P, PRO_COPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
     case PRO_PUPDATE: conv_rows_fwd<P, PRO_PUPDATE><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
     default: conv_rows_fwd<P, PRO_AXPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n); break;
   }
   CISOR_CUDA(cudaGetLastError());
-  if (op.adjoint)
-    conv_cols<P, true><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
-  else
-    conv_cols<P, false><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
+  if (c->cols_nt == 256) {
+    dim3 gcol(P / C::template Col<256>::W, op.ntx);
+    if (op.adjoint)
+      conv_cols<P, true, 256><<<gcol, 256, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
+    else
+      conv_cols<P, false, 256><<<gcol, 256, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
+  } else {
+    dim3 gcol(P / C::template Col<512>::W, op.ntx);
+    if (op.adjoint)
+      conv_cols<P, true, 512><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
+    else
+      conv_cols<P, false, 512><<<gcol, 512, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, n);
+  }
   CISOR_CUDA(cudaGetLastError());
   switch (op.epilogue) {
     case EPI_MATVEC: conv_rows_inv<P, EPI_MATVEC><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, n, c->nblk); break;

@@ -40,7 +40,7 @@ template <int P> struct RPlan {
 // of the plans above (checked by enumeration for P = 64..512):
 //  rows, first exchange : transform b at base b*(P + P/16), one pad slot every 16 elements;
 //  rows, second exchange: same region, bit 3 of the index flipped by bit 6;
-//  columns              : element i of column w at W*(i ^ ((i >> 3) & 1)) + w.
+//  columns              : element i of column w at W*(i ^ ((i >> 3) & 3)) + w.
 struct RowLayA {
   int base;
   __device__ __forceinline__ int operator()(int i) const { return base + i + (i >> 4); }
@@ -51,7 +51,7 @@ struct RowLayB {
 };
 template <int W> struct ColLay {
   int w;
-  __device__ __forceinline__ int operator()(int i) const { return W * (i ^ ((i >> 3) & 1)) + w; }
+  __device__ __forceinline__ int operator()(int i) const { return W * (i ^ ((i >> 3) & 3)) + w; }
 };
 
 // Twiddle table of one plan, stage by stage: stage s (s >= 1, sub-transform

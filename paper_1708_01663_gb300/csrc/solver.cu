@@ -324,37 +324,31 @@ static cisor_status read_active(cisor_ctx* c, int ntx, int* n_active) {
   return CISOR_OK;
 }
 
-cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float2* b, float2* x, int ntx, double tol,
-                         int max_iter, int* iters_max, double* iters_mean, double* resid_max, int* n_bad) {
-  (void)f;  // the operator always reads the context's copy of f (c->f), baked into the graphs
+// Sets the solve parameters, zeroes p and v, forms r = b - A x0, rhat = r and
+// runs the INIT scalar step (all on c->stream).
+static cisor_status init_solve(cisor_ctx* c, int adjoint, const float2* b, float2* x, int ntx, double tol,
+                               int max_iter) {
   const size_t vb = sizeof(float2) * (size_t)ntx * c->N;
-  double hp[2] = {tol, (double)max_iter};
+  // pageable source: the copy is staged before cudaMemcpyAsync returns, so the stack array may go
+  const double hp[2] = {tol, (double)max_iter};
   CISOR_CUDA(cudaMemcpyAsync(c->sparams, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));
   CISOR_CUDA(cudaMemsetAsync(c->p, 0, vb, c->stream));
   CISOR_CUDA(cudaMemsetAsync(c->v, 0, vb, c->stream));
   CISOR_CUDA(cudaMemsetAsync(c->active, 0, sizeof(int) * ntx, c->stream));
   CISOR_TRY(residual_pass(c, adjoint, b, x, ntx));
-  CISOR_TRY(scalar_step(c, SCM_INIT, ntx));
-  int nact = 0;
-  CISOR_TRY(read_active(c, ntx, &nact));
-  cudaGraphExec_t ge = nullptr;
-  int done = 0;
-  for (int restart = 0; restart < 6 && nact > 0; ++restart) {
-    CISOR_TRY(get_graph(c, adjoint, x, ntx, &ge));
-    while (nact > 0 && done < max_iter + c->graph_chunk) {
-      CISOR_CUDA(cudaGraphLaunch(ge, c->stream));
-      c->launches += c->graph_kernels[adjoint];
-      done += c->graph_chunk;
-      CISOR_TRY(read_active(c, ntx, &nact));
-    }
-    CISOR_TRY(residual_pass(c, adjoint, b, x, ntx));
-    CISOR_TRY(scalar_step(c, SCM_TRUE, ntx));
-    CISOR_TRY(read_active(c, ntx, &nact));
-  }
-  if (nact == 0) {
-    // every transmitter ended: refresh the true residuals of those that never iterated
-  }
-  // statistics
+  return scalar_step(c, SCM_INIT, ntx);
+}
+
+// True residual r = b - A x and the restart decision (SCM_TRUE).
+static cisor_status true_residual(cisor_ctx* c, int adjoint, const float2* b, float2* x, int ntx) {
+  CISOR_TRY(residual_pass(c, adjoint, b, x, ntx));
+  return scalar_step(c, SCM_TRUE, ntx);
+}
+
+// Per-transmitter statistics of the last solve; the status reports any
+// transmitter above tol (breakdown or iteration cap).
+static cisor_status collect_stats(cisor_ctx* c, int ntx, double tol, int* iters_max, double* iters_mean,
+                                  double* resid_max, int* n_bad) {
   std::vector<int> it(ntx), fl(ntx);
   std::vector<double> sc((size_t)ntx * SC_STRIDE * 2);
   CISOR_CUDA(cudaMemcpyAsync(it.data(), c->iters, sizeof(int) * ntx, cudaMemcpyDeviceToHost, c->stream));
@@ -382,6 +376,103 @@ cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float
     return brk ? CISOR_ERR_BREAKDOWN : CISOR_ERR_NOT_CONVERGED;
   }
   return CISOR_OK;
+}
+
+cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float2* b, float2* x, int ntx, double tol,
+                         int max_iter, int* iters_max, double* iters_mean, double* resid_max, int* n_bad) {
+  (void)f;  // the operator always reads the context's copy of f (c->f), baked into the graphs
+  CISOR_TRY(init_solve(c, adjoint, b, x, ntx, tol, max_iter));
+  int nact = 0;
+  CISOR_TRY(read_active(c, ntx, &nact));
+  cudaGraphExec_t ge = nullptr;
+  int done = 0;
+  for (int restart = 0; restart < 6 && nact > 0; ++restart) {
+    CISOR_TRY(get_graph(c, adjoint, x, ntx, &ge));
+    while (nact > 0 && done < max_iter + c->graph_chunk) {
+      CISOR_CUDA(cudaGraphLaunch(ge, c->stream));
+      c->launches += c->graph_kernels[adjoint];
+      done += c->graph_chunk;
+      CISOR_TRY(read_active(c, ntx, &nact));
+    }
+    CISOR_TRY(true_residual(c, adjoint, b, x, ntx));
+    CISOR_TRY(read_active(c, ntx, &nact));
+  }
+  return collect_stats(c, ntx, tol, iters_max, iters_mean, resid_max, n_bad);
+}
+
+// ---------------------------------------------------------------- several problems in one graph
+// The problems' BiCGSTAB iterations are captured into ONE graph per chunk:
+// fork from ms.main to every context's stream, each context's chunk of
+// iterations on its own stream, join back.  One cudaGraphLaunch advances all
+// problems; converged transmitters and finished problems exit their CTAs at once.
+cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2* const* b, double tol, int max_iter,
+                         MultiSolve& ms, SolveStat* st) {
+  auto xof = [&](cisor_ctx* c) { return adjoint ? c->vadj : c->u; };
+  for (int i = 0; i < np; ++i) CISOR_TRY(init_solve(cs[i], adjoint, b[i], xof(cs[i]), cs[i]->T, tol, max_iter));
+  auto count = [&](int* total) -> cisor_status {
+    for (int i = 0; i < np; ++i)
+      CISOR_CUDA(cudaMemcpyAsync(cs[i]->h_active, cs[i]->active, sizeof(int) * cs[i]->T, cudaMemcpyDeviceToHost,
+                                 cs[i]->stream));
+    int s = 0;
+    for (int i = 0; i < np; ++i) {
+      CISOR_CUDA(cudaStreamSynchronize(cs[i]->stream));
+      for (int t = 0; t < cs[i]->T; ++t) s += cs[i]->h_active[t];
+    }
+    *total = s;
+    return CISOR_OK;
+  };
+  int nact = 0;
+  CISOR_TRY(count(&nact));
+  if (nact > 0 && !ms.graph[adjoint]) {
+    std::vector<long long> l0(np);
+    for (int i = 0; i < np; ++i) l0[i] = cs[i]->launches;
+    cudaGraph_t g = nullptr;
+    CISOR_CUDA(cudaStreamBeginCapture(ms.main, cudaStreamCaptureModeThreadLocal));
+    cisor_status s = CISOR_OK;
+    cudaError_t e = cudaEventRecord(ms.fork, ms.main);
+    for (int i = 0; i < np && s == CISOR_OK && e == cudaSuccess; ++i) {
+      e = cudaStreamWaitEvent(cs[i]->stream, ms.fork, 0);
+      for (int k = 0; k < cs[i]->graph_chunk && s == CISOR_OK && e == cudaSuccess; ++k)
+        s = enqueue_iteration(cs[i], adjoint, xof(cs[i]), cs[i]->T);
+      if (e == cudaSuccess) e = cudaEventRecord(ms.join[i], cs[i]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ms.main, ms.join[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(ms.main, &g);
+    for (int i = 0; i < np; ++i) {
+      ms.kernels[adjoint][i] = cs[i]->launches - l0[i];
+      cs[i]->launches = l0[i];
+    }
+    if (s != CISOR_OK) {
+      if (e2 == cudaSuccess && g) cudaGraphDestroy(g);
+      return s;
+    }
+    CISOR_CUDA(e);
+    CISOR_CUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&ms.graph[adjoint], g, 0);
+    cudaGraphDestroy(g);
+    CISOR_CUDA(e3);
+  }
+  int done = 0;
+  const int chunk = cs[0]->graph_chunk;
+  for (int restart = 0; restart < 6 && nact > 0; ++restart) {
+    while (nact > 0 && done < max_iter + chunk) {
+      CISOR_CUDA(cudaGraphLaunch(ms.graph[adjoint], ms.main));
+      for (int i = 0; i < np; ++i) cs[i]->launches += ms.kernels[adjoint][i];
+      done += chunk;
+      CISOR_CUDA(cudaStreamSynchronize(ms.main));
+      CISOR_TRY(count(&nact));
+    }
+    for (int i = 0; i < np; ++i) CISOR_TRY(true_residual(cs[i], adjoint, b[i], xof(cs[i]), cs[i]->T));
+    CISOR_TRY(count(&nact));
+  }
+  cisor_status worst = CISOR_OK;
+  for (int i = 0; i < np; ++i) {
+    st[i].status = collect_stats(cs[i], cs[i]->T, tol, &st[i].iters_max, &st[i].iters_mean, &st[i].resid_max,
+                                 &st[i].n_bad);
+    if (st[i].status == CISOR_ERR_CUDA || st[i].status == CISOR_ERR_OOM) return st[i].status;
+    if (st[i].status != CISOR_OK) worst = st[i].status;
+  }
+  return worst;
 }
 
 }  // namespace cisor

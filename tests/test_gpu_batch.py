@@ -1,0 +1,75 @@
+"""Problems of uneven size in one batch (one CUDA-graph launch per iteration chunk)
+against the same problems solved one context at a time, and against the oracle;
+the autotuner's choice leaves results unchanged."""
+import numpy as np
+import pytest
+
+from oracle import grad as ograd
+from oracle import model, solve
+from paper_1708_01663_gb300 import build, cisor, synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(96, 3), (128, 5), (40, 2), (64, 4)]
+
+
+def _geoms():
+    out = []
+    for i, (n, T) in enumerate(SIZES):
+        out.append(dict(n=n, delta=1.0 / 8, tx_angles=synth.plane_wave_angles(T) + 0.1 * i,
+                        rx_pos=synth.circle_receivers(12 + i, 0.75 * n / 8 + 1.0), complex_f=True))
+    return out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_batch_forward_and_grad_match_single_contexts():
+    build.build()
+    geoms = _geoms()
+    batch = cisor.Batch(geoms, autotune=True)
+    fs = [synth.ellipse_phantom(n, 3, (0.0, 0.6), 50 + i, 0.03).astype(np.complex64) for i, (n, _) in enumerate(SIZES)]
+    us = [np.empty((T, n, n), np.complex64) for (n, T) in SIZES]
+    st, infos = batch.forward(fs, us, tol=1e-6, max_iter=3000)
+    ys, gs = [], []
+    for i, g in enumerate(geoms):
+        single = cisor.Cisor(g["n"], g["delta"], g["tx_angles"], g["rx_pos"], complex_f=True)
+        u1 = np.empty_like(us[i])
+        single.forward(fs[i], u_out=u1, tol=1e-6, max_iter=3000)
+        assert _rel(us[i], u1) < 1e-5
+        assert infos[i].resid_max <= 1e-6
+        y = np.empty((single.T, single.M), np.complex64)
+        single.sense(fs[i], u1, y)
+        ys.append((y * (1.0 + 0.1j)).astype(np.complex64))
+        g1 = np.empty((g["n"], g["n"]), np.complex64)
+        D1, _, _ = single.grad(fs[i], ys[i], g1, tol=1e-6, max_iter=3000)
+        gs.append((D1, g1))
+        single.close()
+    grads = [np.empty((n, n), np.complex64) for (n, _) in SIZES]
+    Ds, st, infos = batch.grad(fs, ys, grads, tol=1e-6, max_iter=3000)
+    for i in range(len(SIZES)):
+        assert abs(Ds[i] - gs[i][0]) / gs[i][0] < 1e-5
+        assert _rel(grads[i], gs[i][1]) < 1e-4
+    # oracle fields of the first problem
+    g = geoms[0]
+    prob = model.Problem(g["n"], g["delta"], g["tx_angles"], g["rx_pos"], P=batch.problems[0].P)
+    ref, _, _ = solve.solve_fields(prob, fs[0].astype(np.complex128), prob.u_in, tol=1e-12)
+    assert _rel(us[0], ref) < 1e-4
+    batch.close()
+
+
+def test_autotune_keeps_results():
+    build.build()
+    n, T = 64, 4
+    ctx = cisor.Cisor(n, 1.0 / 8, synth.plane_wave_angles(T), synth.circle_receivers(8, 6.0))
+    f = synth.ellipse_phantom(n, 3, (0.0, 0.5), 3).astype(np.complex64)
+    x = synth.random_field(4, (T, n, n)).astype(np.complex64)
+    y1 = np.empty_like(x)
+    ctx.apply_A(f, x, y1)
+    nt = ctx.autotune(reps=3)
+    assert nt in (256, 512)
+    y2 = np.empty_like(x)
+    ctx.apply_A(f, x, y2)
+    assert _rel(y2, y1) < 1e-6
+    ctx.close()
