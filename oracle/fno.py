@@ -49,12 +49,16 @@ def dft_mats(n, m):
 
 def analysis(v, Fx, Fy):
     """S(v) for v [..., n, n] -> [..., 2m, m]."""
-    return np.einsum("ky,...yx,lx->...kl", Fx, v, Fy)
+    return Fx @ v @ Fy.T
 
 
 def synthesis(Y, Fx, Fy, w, scale):
     """scale * Re sum_{kx,ky} w_ky Y exp(+...) for Y [..., 2m, m] -> [..., n, n]."""
-    return scale * np.real(np.einsum("ky,...kl,lx->...yx", np.conj(Fx), Y * w, np.conj(Fy)))
+    return scale * np.real(np.conj(Fx).T @ (Y * w) @ np.conj(Fy))
+
+
+def _es(sub, *ops):
+    return np.einsum(sub, *ops, optimize=True)
 
 
 def gelu(x):
@@ -93,20 +97,20 @@ def forward(p, f, u_in, L=4):
     m = p["R0"].shape[1]
     Fx, Fy, w = dft_mats(n, m)
     a = features(f, u_in, n)
-    v = np.einsum("oc,cyx->oyx", p["W0"], a) + p["b0"][:, None, None]
+    v = _es("oc,cyx->oyx", p["W0"], a) + p["b0"][:, None, None]
     cache = {"a": a, "v": [v], "X": [], "pre": []}
     for l in range(L):
         X = analysis(v, Fx, Fy)                                      # [C, 2m, m]
-        Ym = np.einsum("klio,ikl->okl", p[f"R{l}"], X)               # [C, 2m, m]
+        Ym = _es("klio,ikl->okl", p[f"R{l}"], X)               # [C, 2m, m]
         s = synthesis(Ym, Fx, Fy, w, 1.0 / (n * n))
-        pre = s + np.einsum("oi,iyx->oyx", p[f"W{l + 1}"], v) + p[f"b{l + 1}"][:, None, None]
+        pre = s + _es("oi,iyx->oyx", p[f"W{l + 1}"], v) + p[f"b{l + 1}"][:, None, None]
         cache["X"].append(X)
         cache["pre"].append(pre)
         v = gelu(pre) if l < L - 1 else pre
         cache["v"].append(v)
-    z = np.einsum("hc,cyx->hyx", p["P1"], v) + p["c1"][:, None, None]
+    z = _es("hc,cyx->hyx", p["P1"], v) + p["c1"][:, None, None]
     h = gelu(z)
-    out = np.einsum("oh,hyx->oyx", p["P2"], h) + p["c2"][:, None, None]
+    out = _es("oh,hyx->oyx", p["P2"], h) + p["c2"][:, None, None]
     cache.update(z=z, h=h)
     return out[0] + 1j * out[1], cache
 
@@ -126,27 +130,27 @@ def loss_and_grad(p, fs, u_ins, targets, L=4):
         total += nd / nt
         dpred = diff / (nd * nt * B)                                  # d loss / d(Re) + j d / d(Im)
         dout = np.stack([dpred.real, dpred.imag])                     # [2, n, n]
-        g["P2"] += np.einsum("oyx,hyx->oh", dout, cache["h"])
+        g["P2"] += _es("oyx,hyx->oh", dout, cache["h"])
         g["c2"] += dout.sum(axis=(1, 2))
-        dh = np.einsum("oh,oyx->hyx", p["P2"], dout)
+        dh = _es("oh,oyx->hyx", p["P2"], dout)
         dz = dh * gelu_grad(cache["z"])
         vL = cache["v"][L]
-        g["P1"] += np.einsum("hyx,cyx->hc", dz, vL)
+        g["P1"] += _es("hyx,cyx->hc", dz, vL)
         g["c1"] += dz.sum(axis=(1, 2))
-        dv = np.einsum("hc,hyx->cyx", p["P1"], dz)
+        dv = _es("hc,hyx->cyx", p["P1"], dz)
         for l in range(L - 1, -1, -1):
             pre = cache["pre"][l]
             dpre = dv * gelu_grad(pre) if l < L - 1 else dv
             vprev = cache["v"][l]
-            g[f"W{l + 1}"] += np.einsum("oyx,iyx->oi", dpre, vprev)
+            g[f"W{l + 1}"] += _es("oyx,iyx->oi", dpre, vprev)
             g[f"b{l + 1}"] += dpre.sum(axis=(1, 2))
-            dv = np.einsum("oi,oyx->iyx", p[f"W{l + 1}"], dpre)
+            dv = _es("oi,oyx->iyx", p[f"W{l + 1}"], dpre)
             dY = analysis(dpre, Fx, Fy) * w / (n * n)                 # adjoint of the synthesis
             X = cache["X"][l]
-            g[f"R{l}"] += np.einsum("ikl,okl->klio", np.conj(X), dY)
-            dX = np.einsum("klio,okl->ikl", np.conj(p[f"R{l}"]), dY)
+            g[f"R{l}"] += _es("ikl,okl->klio", np.conj(X), dY)
+            dX = _es("klio,okl->ikl", np.conj(p[f"R{l}"]), dY)
             dv += synthesis(dX, Fx, Fy, np.ones_like(w), 1.0)          # adjoint of the analysis
-        g["W0"] += np.einsum("oyx,cyx->oc", dv, cache["a"])
+        g["W0"] += _es("oyx,cyx->oc", dv, cache["a"])
         g["b0"] += dv.sum(axis=(1, 2))
     return total / B, g
 

@@ -93,6 +93,15 @@ def load(path: str = LIB_PATH):
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
         "cisor_data_term": [vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_autotune": [vp, i, POINTER(c_int)],
+        "cisor_fno_create": [POINTER(c_void_p), i, ctypes.c_ulonglong, vp],
+        "cisor_fno_destroy": [vp],
+        "cisor_fno_num_params": [vp, POINTER(c_longlong)],
+        "cisor_fno_get_params": [vp, vp, i],
+        "cisor_fno_set_params": [vp, vp],
+        "cisor_fno_forward": [vp, vp, i, vp, i, vp],
+        "cisor_fno_loss_grad": [vp, vp, i, vp, vp, i, POINTER(c_double), vp],
+        "cisor_fno_train_step": [vp, vp, i, vp, vp, i, d, POINTER(c_double)],
+        "cisor_fno_warm_start": [vp, vp, vp, vp],
         "cisor_batch_create": [POINTER(c_void_p), POINTER(Geometry), i, vp, i],
         "cisor_batch_destroy": [vp],
         "cisor_batch_context": [vp, i, POINTER(c_void_p)],
@@ -365,3 +374,93 @@ class Batch:
                                         self._ptrs(grad_out, [p.N for p in ps]), D, ctypes.byref(opts), infos)
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return list(D), st, list(infos)
+
+
+FNO_N = 128
+
+
+class FNO:
+    """Learned warm start (cisor_fno_*): a 128 x 128 Fourier neural operator."""
+
+    def __init__(self, max_batch=32, seed=0, stream=None):
+        lib = load()
+        self._lib = lib
+        self._h = c_void_p()
+        self.stream = _current_stream() if stream is None else stream
+        _check(lib.cisor_fno_create(ctypes.byref(self._h), int(max_batch), int(seed), self.stream))
+        cnt = c_longlong()
+        _check(lib.cisor_fno_num_params(self._h, ctypes.byref(cnt)))
+        self.num_params = cnt.value
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cisor_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, out, as_used=True):
+        return _check(self._lib.cisor_fno_get_params(self._h, ptr(out, self.num_params, "float32"), int(as_used)))
+
+    def set_params(self, arr):
+        return _check(self._lib.cisor_fno_set_params(self._h, ptr(arr, self.num_params, "float32")))
+
+    def forward(self, f, u_in, out, f_per_sample=True):
+        B = (u_in.numel() if hasattr(u_in, "numel") else u_in.size) // (FNO_N * FNO_N)
+        nf = B if f_per_sample else 1
+        return _check(self._lib.cisor_fno_forward(self._h, ptr(f, nf * FNO_N * FNO_N), int(f_per_sample),
+                                                  ptr(u_in, B * FNO_N * FNO_N), B, ptr(out, B * FNO_N * FNO_N)))
+
+    def loss_grad(self, f, u_in, target, grad_out=None, f_per_sample=True):
+        B = (u_in.numel() if hasattr(u_in, "numel") else u_in.size) // (FNO_N * FNO_N)
+        nf = B if f_per_sample else 1
+        loss = c_double()
+        _check(self._lib.cisor_fno_loss_grad(self._h, ptr(f, nf * FNO_N * FNO_N), int(f_per_sample),
+                                             ptr(u_in, B * FNO_N * FNO_N), ptr(target, B * FNO_N * FNO_N), B,
+                                             ctypes.byref(loss),
+                                             ptr(grad_out, self.num_params, "float32") if grad_out is not None
+                                             else None))
+        return loss.value
+
+    def train_step(self, f, u_in, target, lr, f_per_sample=True):
+        B = (u_in.numel() if hasattr(u_in, "numel") else u_in.size) // (FNO_N * FNO_N)
+        nf = B if f_per_sample else 1
+        loss = c_double()
+        _check(self._lib.cisor_fno_train_step(self._h, ptr(f, nf * FNO_N * FNO_N), int(f_per_sample),
+                                              ptr(u_in, B * FNO_N * FNO_N), ptr(target, B * FNO_N * FNO_N), B,
+                                              float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def warm_start(self, ctx, f, x0_out):
+        return _check(self._lib.cisor_fno_warm_start(self._h, ctx._ctx, ptr(f, ctx.N), ptr(x0_out, ctx.T * ctx.N)))
+
+
+def fno_param_dict(flat, C=32, m=16, L=4, H=128):
+    """Split a flat parameter array into named arrays (FP64, complex spectral weights)."""
+    flat = np.asarray(flat, dtype=np.float64)
+    out, o = {}, 0
+
+    def take(name, shape, cplx=False):
+        nonlocal o
+        cnt = int(np.prod(shape)) * (2 if cplx else 1)
+        a = flat[o:o + cnt]
+        o += cnt
+        out[name] = (a[0::2] + 1j * a[1::2]).reshape(shape) if cplx else a.reshape(shape)
+
+    take("W0", (C, 6))
+    take("b0", (C,))
+    for l in range(L):
+        take(f"R{l}", (2 * m, m, C, C), True)
+        take(f"W{l + 1}", (C, C))
+        take(f"b{l + 1}", (C,))
+    take("P1", (H, C))
+    take("c1", (H,))
+    take("P2", (2, H))
+    take("c2", (2,))
+    assert o == flat.size
+    return out
