@@ -239,13 +239,16 @@ cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* 
 
 /* ---- Learned warm start (not in the paper) ----
  * A Fourier neural operator predicts the scattered field u - u_in of the
- * field solve A u = u_in from (f, u_in) on 128 x 128 grids: 6 input channels
- * (Re f, Im f, Re u_in, Im u_in, x, y), 1x1 lifting to width 32, four Fourier
+ * field solve A u = u_in from (f, u_in) on 128 x 128 grids: 8 input channels
+ * (Re f, Im f, Re u_in, Im u_in, the unit local propagation direction of
+ * u_in from its phase gradient, x, y), 1x1 lifting to width 32, four Fourier
  * layers (16 x 32 retained modes, 1x1 skip, GELU), projection 32 -> 128 -> 2.
+ * The network output e is the demodulated scattered field: u - u_in is
+ * predicted as u_in * e (targets are conj(u_in) (u - u_in)).
  * Weights are FP32 masters with a BF16 copy that every kernel reads;
  * activations and accumulation are FP32.  The prediction only seeds x0 of the
  * solve (x0_mode 1), which still stops on the true residual.  Parameter
- * arrays are [cisor_fno_num_params] floats in the layout W0 [32x6], b0 [32],
+ * arrays are [cisor_fno_num_params] floats in the layout W0 [32x8], b0 [32],
  * per layer l: R_l [32 kx][16 ky][32 in][32 out] complex, W_l [32x32], b_l
  * [32]; then P1 [128x32], c1 [128], P2 [2x128], c2 [2]. */
 typedef struct cisor_fno cisor_fno;
@@ -262,7 +265,7 @@ cisor_status cisor_fno_get_params(cisor_fno* fno, float* out, int as_used);
 /* Replace the FP32 masters (and the BF16 copy); resets the Adam state. */
 cisor_status cisor_fno_set_params(cisor_fno* fno, const float* in);
 
-/* u_sc_out [B, 16384] = network(f, u_in) for B samples; f is [B, 16384]
+/* u_sc_out [B, 16384] = network output e(f, u_in) for B samples; f is [B, 16384]
  * (f_per_sample = 1) or one [16384] image shared by all samples (0);
  * u_in [B, 16384]; complex64. */
 cisor_status cisor_fno_forward(cisor_fno* fno, const void* f, int f_per_sample, const void* u_in, int B,
@@ -278,7 +281,7 @@ cisor_status cisor_fno_loss_grad(cisor_fno* fno, const void* f, int f_per_sample
 cisor_status cisor_fno_train_step(cisor_fno* fno, const void* f, int f_per_sample, const void* u_in,
                                   const void* target, int B, double lr, double* loss);
 
-/* x0_out [T, N] = u_in + network(f, u_in) for every transmitter of a context
+/* x0_out [T, N] = u_in (1 + e(f, u_in)) for every transmitter of a context
  * with a 128 x 128 grid: the warm start for cisor_forward's x0 (x0_mode 1). */
 cisor_status cisor_fno_warm_start(cisor_fno* fno, cisor_ctx* ctx, const void* f, void* x0_out);
 

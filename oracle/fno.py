@@ -6,14 +6,18 @@ network the CUDA kernels implement, with a hand-written backward pass, used
 to check the GPU forward values and parameter gradients.
 
 Network for one sample (grid n x n, width C, m modes, L layers, hidden H):
-  features   a = (Re f, Im f, Re u_in, Im u_in, x, y)            6 x n x n
+  features   a = (Re f, Im f, Re u_in, Im u_in, d_x, d_y, x, y)  8 x n x n
+             d = local propagation direction of u_in: the unit vector along
+             (Im(conj u g_x), Im(conj u g_y)), g = central differences with
+             clamped edges (0 where that vector vanishes)
   lifting    v0 = W0 a + b0                                       C x n x n (1x1 conv)
   layer l    X  = S(v_{l-1})      truncated DFT, per channel      C x 2m x m complex
              Y[o] = sum_i R_l[:, :, i, o] X[i]                    per mode
              pre = Lsyn(Y) + W_l v_{l-1} + b_l
              v_l = GELU(pre)  (no GELU after the last layer)
   projection z = P1 v_L + c1, h = GELU(z), out = P2 h + c2         2 x n x n
-  output     u_sc = out[0] + j out[1]
+  output     e = out[0] + j out[1]; the warm start predicts u_sc = u_in * e
+             (targets are the demodulated fields conj(u_in) u_sc)
 S keeps the frequencies kx in {0..m-1, n-m..n-1} along rows (iy) and
 ky in {0..m-1} along columns (ix):
   S(v)[kx, ky] = sum_{iy, ix} v[iy, ix] exp(-2 pi j (kx iy + ky ix) / n),
@@ -69,17 +73,30 @@ def gelu_grad(x):
     return 0.5 * (1.0 + special.erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
+def direction(u):
+    """Unit local propagation direction of a field from its phase gradient."""
+    up = np.pad(u, 1, mode="edge")
+    gx = (up[1:-1, 2:] - up[1:-1, :-2]) / 2.0
+    gy = (up[2:, 1:-1] - up[:-2, 1:-1]) / 2.0
+    vx = np.imag(np.conj(u) * gx)
+    vy = np.imag(np.conj(u) * gy)
+    nv = np.sqrt(vx * vx + vy * vy)
+    safe = np.where(nv > 0, nv, 1.0)
+    return np.where(nv > 0, vx / safe, 0.0), np.where(nv > 0, vy / safe, 0.0)
+
+
 def features(f, u_in, n):
     c = (np.arange(n) + 0.5) / n - 0.5
     Y, X = np.meshgrid(c, c, indexing="ij")
-    return np.stack([f.real, f.imag, u_in.real, u_in.imag, X, Y])
+    dx, dy = direction(u_in)
+    return np.stack([f.real, f.imag, u_in.real, u_in.imag, dx, dy, X, Y])
 
 
 def init_params(n=128, C=32, m=16, L=4, H=128, seed=0):
     """Seeded initial parameters (same recipe as the CUDA initialiser is NOT required:
     tests pass the GPU's parameters in)."""
     rng = np.random.default_rng(seed)
-    p = {"W0": rng.uniform(-1, 1, (C, 6)) / math.sqrt(6), "b0": np.zeros(C)}
+    p = {"W0": rng.uniform(-1, 1, (C, 8)) / math.sqrt(8), "b0": np.zeros(C)}
     for l in range(L):
         p[f"R{l}"] = (rng.uniform(-1, 1, (2 * m, m, C, C)) + 1j * rng.uniform(-1, 1, (2 * m, m, C, C))) / C
         p[f"W{l + 1}"] = rng.uniform(-1, 1, (C, C)) / math.sqrt(C)

@@ -452,7 +452,7 @@ def fno_param_dict(flat, C=32, m=16, L=4, H=128):
         o += cnt
         out[name] = (a[0::2] + 1j * a[1::2]).reshape(shape) if cplx else a.reshape(shape)
 
-    take("W0", (C, 6))
+    take("W0", (C, 8))
     take("b0", (C,))
     for l in range(L):
         take(f"R{l}", (2 * m, m, C, C), True)

@@ -5,10 +5,15 @@
 // initial guess x0 for A u = u_in).
 //
 // Network (grid 128 x 128, width 32, 16 modes, 4 Fourier layers, hidden 128):
-//   a  = (Re f, Im f, Re u_in, Im u_in, x, y)          6 channels
+//   a  = (Re f, Im f, Re u_in, Im u_in, d_x, d_y, x, y)  8 channels; d is the
+//        unit local propagation direction of u_in (phase gradient by central
+//        differences, clamped at the edges)
 //   v0 = W0 a + b0                                       1x1 lifting
 //   v_l = GELU(Lsyn(R_l . S(v_{l-1})) + W_l v_{l-1} + b_l)  (no GELU on the last)
-//   out = P2 GELU(P1 v_4 + c1) + c2,  u_sc = out_0 + j out_1
+//   out = P2 GELU(P1 v_4 + c1) + c2,  e = out_0 + j out_1, predicted u - u_in = u_in e
+// (the demodulated target keeps forward-scattered energy at low frequencies,
+// inside the 16 retained modes; the incident carrier itself sits at 16 cycles
+// per side at lambda/8)
 // S keeps kx in {0..15, 112..127} (rows) x ky in {0..15} (columns) of the
 // 2D DFT; Lsyn is (1/128^2) Re of the truncated inverse with weight 2 on
 // ky > 0.  Loss: mean over samples of ||out - t|| / ||t||.
@@ -27,7 +32,8 @@ namespace cisor {
 
 constexpr int FN = 128, FNN = FN * FN, FC = 32, FM = 16, FKX = 2 * FM, FMODES = FKX * FM, FH = 128, FL = 4;
 constexpr long long F_LAYER = (long long)FMODES * FC * FC * 2 + FC * FC + FC;  // floats per Fourier layer
-constexpr long long F_W0 = 0, F_B0 = FC * 6, F_LAYERS = F_B0 + FC;
+constexpr int FIN = 8;  // input channels
+constexpr long long F_W0 = 0, F_B0 = FC * FIN, F_LAYERS = F_B0 + FC;
 constexpr long long F_P1 = F_LAYERS + FL * F_LAYER, F_C1 = F_P1 + FH * FC, F_P2 = F_C1 + FH, F_C2 = F_P2 + 2 * FH;
 constexpr long long F_TOTAL = F_C2 + 2;
 __host__ __device__ constexpr long long f_R(int l) { return F_LAYERS + l * F_LAYER; }
@@ -44,8 +50,8 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 __global__ void fno_features_lift(const float2* __restrict__ f, int f_per_sample, const float2* __restrict__ u_in,
                                   const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ pm, int B,
                                   float* __restrict__ feat, float* __restrict__ v0) {
-  __shared__ float W[FC * 6], bb[FC];
-  for (int i = threadIdx.x; i < FC * 6; i += blockDim.x) W[i] = __bfloat162float(wbf[F_W0 + i]);
+  __shared__ float W[FC * FIN], bb[FC];
+  for (int i = threadIdx.x; i < FC * FIN; i += blockDim.x) W[i] = __bfloat162float(wbf[F_W0 + i]);
   for (int i = threadIdx.x; i < FC; i += blockDim.x) bb[i] = pm[F_B0 + i];
   __syncthreads();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,15 +59,22 @@ __global__ void fno_features_lift(const float2* __restrict__ f, int f_per_sample
   const int b = (int)(idx / FNN), pix = (int)(idx % FNN);
   const int iy = pix / FN, ix = pix % FN;
   const float2 fv = f[(f_per_sample ? (long long)b * FNN : 0) + pix];
-  const float2 u = u_in[(long long)b * FNN + pix];
-  const float a[6] = {fv.x, fv.y, u.x, u.y, (ix + 0.5f) / FN - 0.5f, (iy + 0.5f) / FN - 0.5f};
+  const float2* ub = u_in + (long long)b * FNN;
+  const float2 u = ub[pix];
+  // central differences, clamped at the edges
+  const float2 gx = c_scale(c_sub(ub[iy * FN + min(ix + 1, FN - 1)], ub[iy * FN + max(ix - 1, 0)]), 0.5f);
+  const float2 gy = c_scale(c_sub(ub[min(iy + 1, FN - 1) * FN + ix], ub[max(iy - 1, 0) * FN + ix]), 0.5f);
+  const float vx = c_cjmul(u, gx).y, vy = c_cjmul(u, gy).y;
+  const float nv = sqrtf(vx * vx + vy * vy);
+  const float dx = nv > 0.f ? vx / nv : 0.f, dy = nv > 0.f ? vy / nv : 0.f;
+  const float a[FIN] = {fv.x, fv.y, u.x, u.y, dx, dy, (ix + 0.5f) / FN - 0.5f, (iy + 0.5f) / FN - 0.5f};
 #pragma unroll
-  for (int k = 0; k < 6; ++k) feat[((long long)b * 6 + k) * FNN + pix] = a[k];
+  for (int k = 0; k < FIN; ++k) feat[((long long)b * FIN + k) * FNN + pix] = a[k];
 #pragma unroll 4
   for (int c = 0; c < FC; ++c) {
     float s = bb[c];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s += W[c * 6 + k] * a[k];
+    for (int k = 0; k < FIN; ++k) s += W[c * FIN + k] * a[k];
     v0[((long long)b * FC + c) * FNN + pix] = s;
   }
 }
@@ -308,6 +321,113 @@ __global__ void __launch_bounds__(128) fno_proj_fwd(const float* __restrict__ vL
   out[b * FNN + pix] = make_float2(o0, o1);
 }
 
+// Tensor-core projection: z = P1 v + c1 on mma.sync m16n8k16 (BF16 operands,
+// FP32 accumulation), h = GELU(z), out = P2 h + c2.  A warp owns 16 pixels x
+// 128 hidden units (16 n-tiles, K = 32 channels in two k-steps).  Activations
+// are split into BF16 hi + lo parts (two MMAs), so the product keeps ~16
+// mantissa bits of v; the BF16 weights are exact.  store != 0 keeps z and h
+// for the backward pass.
+__device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_col));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_col));
+  return a | (b << 16);
+}
+__device__ __forceinline__ float bf16_residual(float x) { return x - __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int STORE>
+__global__ void __launch_bounds__(128) fno_proj_fwd_tc(const float* __restrict__ vL,
+                                                       const __nv_bfloat16* __restrict__ wbf,
+                                                       const float* __restrict__ pm, int B, float* __restrict__ z,
+                                                       float* __restrict__ h, float2* __restrict__ out) {
+  __shared__ uint32_t P1w[FH * FC / 2];  // P1[n][k] as bf16 pairs along k
+  __shared__ float P2s[2 * FH], c1s[FH];
+  const uint32_t* p1g = reinterpret_cast<const uint32_t*>(wbf + F_P1);
+  for (int i = threadIdx.x; i < FH * FC / 2; i += 128) P1w[i] = p1g[i];
+  for (int i = threadIdx.x; i < 2 * FH; i += 128) P2s[i] = __bfloat162float(wbf[F_P2 + i]);
+  for (int i = threadIdx.x; i < FH; i += 128) c1s[i] = pm[F_C1 + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const long long P0 = ((long long)blockIdx.x * 4 + warp) * 16;  // first pixel of this warp
+  if (P0 >= (long long)B * FNN) return;
+  const long long b = P0 / FNN;
+  const int pix0 = (int)(P0 % FNN);  // 16 pixels never straddle samples (FNN % 16 == 0)
+  const float* vb = vL + b * FC * FNN + pix0;
+  // A fragments (hi and lo) for the two k-steps
+  uint32_t ahi[2][4], alo[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    const int k0 = ks * 16 + 2 * t;
+    float x[8];
+    x[0] = vb[(long long)(k0)*FNN + g];
+    x[1] = vb[(long long)(k0 + 1) * FNN + g];
+    x[2] = vb[(long long)(k0)*FNN + g + 8];
+    x[3] = vb[(long long)(k0 + 1) * FNN + g + 8];
+    x[4] = vb[(long long)(k0 + 8) * FNN + g];
+    x[5] = vb[(long long)(k0 + 9) * FNN + g];
+    x[6] = vb[(long long)(k0 + 8) * FNN + g + 8];
+    x[7] = vb[(long long)(k0 + 9) * FNN + g + 8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      ahi[ks][r] = pack_bf16(x[2 * r], x[2 * r + 1]);
+      alo[ks][r] = pack_bf16(bf16_residual(x[2 * r]), bf16_residual(x[2 * r + 1]));
+    }
+  }
+  float o0a = 0.f, o1a = 0.f, o0b = 0.f, o1b = 0.f;  // outputs of pixels g (a) and g + 8 (b)
+#pragma unroll 4
+  for (int j = 0; j < FH / 8; ++j) {
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int n = 8 * j + g;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const uint32_t b0 = P1w[n * (FC / 2) + ks * 8 + t];      // k = ks*16 + 2t, 2t+1
+      const uint32_t b1 = P1w[n * (FC / 2) + ks * 8 + 4 + t];  // k + 8
+      mma_bf16_16816(d, ahi[ks], b0, b1);
+      mma_bf16_16816(d, alo[ks], b0, b1);
+    }
+    // d[0], d[1]: pixel g, hidden 8j + 2t, +1 ; d[2], d[3]: pixel g + 8
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int hh = 8 * j + 2 * t + (e & 1);
+      const int px = g + (e >> 1) * 8;
+      const float zz = d[e] + c1s[hh];
+      const float hv = gelu_f(zz);
+      if (STORE) {
+        z[(b * FH + hh) * FNN + pix0 + px] = zz;
+        h[(b * FH + hh) * FNN + pix0 + px] = hv;
+      }
+      if (e < 2) {
+        o0a += P2s[hh] * hv;
+        o1a += P2s[FH + hh] * hv;
+      } else {
+        o0b += P2s[hh] * hv;
+        o1b += P2s[FH + hh] * hv;
+      }
+    }
+  }
+  // sum over the four lanes (t) that share a pixel row g
+#pragma unroll
+  for (int m = 1; m < 4; m <<= 1) {
+    o0a += __shfl_xor_sync(0xffffffffu, o0a, m);
+    o1a += __shfl_xor_sync(0xffffffffu, o1a, m);
+    o0b += __shfl_xor_sync(0xffffffffu, o0b, m);
+    o1b += __shfl_xor_sync(0xffffffffu, o1b, m);
+  }
+  if (t == 0) {
+    const float c20 = pm[F_C2], c21 = pm[F_C2 + 1];
+    out[b * FNN + pix0 + g] = make_float2(o0a + c20, o1a + c21);
+    out[b * FNN + pix0 + g + 8] = make_float2(o0b + c20, o1b + c21);
+  }
+}
+
 // dz = (P2^T dout) * GELU'(z) (overwrites z), dv = P1^T dz; one thread per pixel.
 __global__ void __launch_bounds__(128) fno_proj_bwd(const float* __restrict__ dout, float* __restrict__ z,
                                                     const __nv_bfloat16* __restrict__ wbf, int B,
@@ -455,11 +575,11 @@ __global__ void fno_adam(float* __restrict__ pm, const float* __restrict__ g, fl
   wbf[i] = __float2bfloat16_rn(p);
 }
 
-// x0 = u_in + u_sc
-__global__ void fno_add_incident(const float2* __restrict__ u_in, const float2* __restrict__ usc,
+// x0 = u_in + u_in e (e = demodulated scattered field)
+__global__ void fno_add_incident(const float2* __restrict__ u_in, const float2* __restrict__ e,
                                  float2* __restrict__ x0, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x0[i] = c_add(u_in[i], usc[i]);
+  if (i < n) x0[i] = c_add(u_in[i], c_mul(u_in[i], e[i]));
 }
 
 // Seeded initialisation (SplitMix64 per element): weights uniform in
@@ -476,7 +596,7 @@ __global__ void fno_init(float* __restrict__ pm, long long n, unsigned long long
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float scale = 0.f;
-  if (i < F_B0) scale = 0.40824829f;  // 1/sqrt(6)
+  if (i < F_B0) scale = 0.35355339f;  // 1/sqrt(8)
   else if (i >= F_P1 && i < F_C1) scale = 0.17677670f;  // 1/sqrt(32)
   else if (i >= F_P2 && i < F_C2) scale = 0.08838835f;  // 1/sqrt(128)
   else if (i >= F_LAYERS && i < F_P1) {
@@ -521,8 +641,9 @@ cisor_status fno_leave(cisor_fno* F) {
 
 unsigned grid_of(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// forward pass on F->fbuf / F->ubuf (f_per_sample as given), leaves F->out
-cisor_status fno_forward_core(cisor_fno* F, int fps, int B) {
+// forward pass on F->fbuf / F->ubuf (f_per_sample as given), leaves F->out;
+// store keeps the projection's z and h for a backward pass
+cisor_status fno_forward_core(cisor_fno* F, int fps, int B, int store = 1) {
   cudaStream_t s = F->stream;
   const long long BP = (long long)B * FNN;
   fno_features_lift<<<grid_of(BP, 256), 256, 0, s>>>(F->fbuf, fps, F->ubuf, F->wbf, F->pm, B, F->feat, F->v[0]);
@@ -538,7 +659,10 @@ cisor_status fno_forward_core(cisor_fno* F, int fps, int B) {
                                                        l < FL - 1, F->v[l + 1]);
     CISOR_CUDA(cudaGetLastError());
   }
-  fno_proj_fwd<<<grid_of(BP, 128), 128, 0, s>>>(F->v[FL], F->wbf, F->pm, B, F->z, F->h, F->out);
+  if (store)
+    fno_proj_fwd_tc<1><<<grid_of(BP, 64), 128, 0, s>>>(F->v[FL], F->wbf, F->pm, B, F->z, F->h, F->out);
+  else
+    fno_proj_fwd_tc<0><<<grid_of(BP, 64), 128, 0, s>>>(F->v[FL], F->wbf, F->pm, B, F->z, F->h, F->out);
   CISOR_CUDA(cudaGetLastError());
   return CISOR_OK;
 }
@@ -574,7 +698,7 @@ cisor_status fno_backward_core(cisor_fno* F, int B) {
     dv = dvn;
     dvn = t;
   }
-  fno_outer<FC, 6><<<gch, 256, 0, s>>>(dv, F->feat, B, F->grad + F_W0, F->grad + F_B0);
+  fno_outer<FC, FIN><<<gch, 256, 0, s>>>(dv, F->feat, B, F->grad + F_W0, F->grad + F_B0);
   CISOR_CUDA(cudaGetLastError());
   return CISOR_OK;
 }
@@ -660,7 +784,7 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
   } allocs[] = {{(void**)&F->pm, sizeof(float) * F_TOTAL}, {(void**)&F->grad, sizeof(float) * F_TOTAL},
                 {(void**)&F->m1, sizeof(float) * F_TOTAL},  {(void**)&F->m2, sizeof(float) * F_TOTAL},
                 {(void**)&F->wbf, sizeof(__nv_bfloat16) * F_TOTAL}, {(void**)&F->twst, sizeof(float2) * 2 * TW_STRIDE},
-                {(void**)&F->feat, sizeof(float) * (size_t)max_batch * 6 * FNN}, {(void**)&F->z, hid},
+                {(void**)&F->feat, sizeof(float) * (size_t)max_batch * FIN * FNN}, {(void**)&F->z, hid},
                 {(void**)&F->h, hid}, {(void**)&F->dout, sizeof(float) * (size_t)max_batch * 2 * FNN},
                 {(void**)&F->dvA, act}, {(void**)&F->dvB, act}, {(void**)&F->dpre, act},
                 {(void**)&F->loss, sizeof(float) * max_batch}, {(void**)&F->Y, md}, {(void**)&F->dY, md},
@@ -752,7 +876,7 @@ cisor_status cisor_fno_forward(cisor_fno* F, const void* f, int f_per_sample, co
   if (bad_batch(F, B)) return CISOR_ERR_INVALID_ARG;
   CISOR_TRY(fno_enter(F));
   CISOR_TRY(stage_inputs(F, f, f_per_sample, u_in, nullptr, B));
-  CISOR_TRY(fno_forward_core(F, f_per_sample, B));
+  CISOR_TRY(fno_forward_core(F, f_per_sample, B, 0));
   CISOR_CUDA(cudaMemcpyAsync(u_sc_out, F->out, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
   CISOR_CUDA(cudaStreamSynchronize(F->stream));
   return fno_leave(F);
@@ -809,7 +933,7 @@ cisor_status cisor_fno_warm_start(cisor_fno* F, cisor_ctx* c, const void* f, voi
   CISOR_TRY(fno_enter(F));
   CISOR_CUDA(cudaMemcpyAsync(F->fbuf, f, sizeof(float2) * FNN, cudaMemcpyDefault, F->stream));
   CISOR_CUDA(cudaMemcpyAsync(F->ubuf, c->u_in, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDeviceToDevice, F->stream));
-  CISOR_TRY(fno_forward_core(F, 0, B));
+  CISOR_TRY(fno_forward_core(F, 0, B, 0));
   fno_add_incident<<<grid_of((long long)B * FNN, 256), 256, 0, F->stream>>>(F->ubuf, F->out, F->usc, (long long)B * FNN);
   CISOR_CUDA(cudaGetLastError());
   CISOR_CUDA(cudaMemcpyAsync(x0_out, F->usc, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
