@@ -212,6 +212,7 @@ def main():
     n, T, M = cfg["n"], cfg["T"], cfg["M"]
     complex_f = cfg["imag"] != 0.0
     ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f)
+    cols_nt = ctx.autotune(reps=10)  # pick the column-FFT CTA shape by measurement
 
     # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
     f_dev = torch.from_numpy(np.ascontiguousarray(f_true, dtype=np.complex64)).to(dev)
@@ -335,6 +336,7 @@ def main():
                        "solves_per_step": solves_per_step, "start": "cold (u_in / 0)",
                        "l2": "working set > L2 (Krylov vectors 12 x 32 MB)",
                        "parallelism": "independent replicas" if ws > 1 else "single GPU",
+                       "autotuned_cols_cta": cols_nt,
                        "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
                        "fwd_iters_max": max(i["iters_max"] for i in step_infos) if step_infos else None,
                        "adj_iters_max": max(i["adj_iters_max"] for i in step_infos) if step_infos else None,

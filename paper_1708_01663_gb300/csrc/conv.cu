@@ -199,14 +199,27 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   for (int q = 0; q < 8 / R0; ++q)
 #pragma unroll
     for (int r = 0; r < R0; ++r) v[q * R0 + r] = rowok ? srow[PL::elem(lt, q, r, R0)] : make_float2(0.f, 0.f);
-  reg_fft<P, true, true>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
   const bool postf = op.mul_f && op.adjoint;
   const bool any_dot = (op.dot_a[0] | op.dot_a[1] | op.dot_a[2]) != 0;
   const bool aux0 = EPI == EPI_MATVEC && (op.dot_a[0] == OP_AUX || op.dot_b[0] == OP_AUX);
+  const bool need_aux = EPI == EPI_RESID || aux0 || (EPI == EPI_CONV_ADD && op.aux);
+  constexpr int RL = PL::template last<true>();
+  // epilogue operands are loaded before the transform so their latency overlaps it
+  float2 pre_src[8], pre_aux[8];
+#pragma unroll
+  for (int q = 0; q < 8 / RL; ++q)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int ix = PL::elem(lt, q, r, RL);
+      const bool ok = rowok && ix < n;
+      const long long idx = tx * N + (long long)(rowok ? iy : 0) * n + (ix < n ? ix : 0);
+      pre_src[q * RL + r] = (ok && EPI != EPI_CONV_ADD) ? op.esrc[idx] : make_float2(0.f, 0.f);
+      pre_aux[q * RL + r] = (ok && need_aux) ? op.aux[idx] : make_float2(0.f, 0.f);
+    }
+  reg_fft<P, true, true>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
   float2 acc[DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) acc[s] = make_float2(0.f, 0.f);
-  constexpr int RL = PL::template last<true>();
   if (rowok) {
 #pragma unroll
     for (int q = 0; q < 8 / RL; ++q)
@@ -218,17 +231,13 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
         const long long idx = tx * N + pix;
         float2 c = v[q * RL + r];
         if (postf) c = c_cjmul(op.f[pix], c);
-        float2 src = make_float2(0.f, 0.f), aux = src, y;
+        const float2 src = pre_src[q * RL + r], aux = pre_aux[q * RL + r];
+        float2 y;
         if (EPI == EPI_MATVEC) {
-          src = op.esrc[idx];
           y = c_sub(src, c);
-          if (aux0) aux = op.aux[idx];
         } else if (EPI == EPI_RESID) {
-          src = op.esrc[idx];
-          aux = op.aux[idx];
           y = c_sub(aux, c_sub(src, c));
         } else {
-          if (op.aux) aux = op.aux[idx];
           y = c_add(c, aux);
         }
         op.out[idx] = y;

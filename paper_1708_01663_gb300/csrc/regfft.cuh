@@ -68,6 +68,9 @@ template <int P, bool REV> struct TwTable {
 };
 constexpr int TW_STRIDE = 512;  // floats2 reserved per plan table
 
+// One stage on the thread's registers.  Only w = tws[k] (the r = 1 row of
+// the stage table) is read from shared memory; w^2 .. w^7 are formed by
+// complex products (depth 3), trading shared-memory loads for FMAs.
 template <int P, int R, int NS, bool INV>
 __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __restrict__ tws) {
   constexpr int NTF = P / 8;
@@ -76,12 +79,22 @@ __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __re
     if constexpr (NS > 1) {
       const int j = t + q * NTF;
       const int k = j & (NS - 1);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = tws[(r - 1) * NS + k];
-        if (INV) w.y = -w.y;
-        v[q * R + r] = c_mul(v[q * R + r], w);
+      float2 w1 = tws[k];
+      if (INV) w1.y = -w1.y;
+      float2 w[8];
+      w[1] = w1;
+      if constexpr (R >= 4) {
+        w[2] = c_mul(w1, w1);
+        w[3] = c_mul(w[2], w1);
       }
+      if constexpr (R == 8) {
+        w[4] = c_mul(w[2], w[2]);
+        w[5] = c_mul(w[4], w1);
+        w[6] = c_mul(w[4], w[2]);
+        w[7] = c_mul(w[4], w[3]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = c_mul(v[q * R + r], w[r]);
     }
     dft_r<R, INV>(v + q * R);
   }
