@@ -34,10 +34,10 @@ def data_and_grad(prob, f, y, tol=1e-10, u0=None, v0=None, return_fields=False):
     u, Z, _, _ = forward(prob, f, tol, x0=u0)
     w = Z - y
     D = 0.5 * float(np.sum(np.abs(w) ** 2))
-    z = (w @ np.conj(prob.H)).reshape(-1, n, n)       # H^H w_t for each t
+    z = (w @ np.conj(prob.H)).reshape((-1,) + f.shape)  # H^H w_t for each t
     b = np.conj(f)[None] * z
     v, _, _ = solve_fields(prob, f, b, x0=v0, tol=tol, adjoint=True)
-    g = np.zeros((n, n), dtype=np.complex128)
+    g = np.zeros(f.shape, dtype=np.complex128)
     for t in range(prob.T):
         g += np.conj(u[t]) * (z[t] + conv_G(v[t], prob.ghat, n, adjoint=True))
     if return_fields:

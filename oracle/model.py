@@ -155,6 +155,15 @@ def plane_waves(angles: np.ndarray, n: int, delta: float, kb: float) -> np.ndarr
     return np.exp(1j * kb * (np.cos(th) * X[None] + np.sin(th) * Y[None]))
 
 
+def plane_waves_3d(dirs: np.ndarray, n: int, delta: float, kb: float) -> np.ndarray:
+    """[T, n, n, n] incident plane waves exp(j kb d_t . r) for unit directions d_t [T, 3]."""
+    c = axis_centres(n, delta)
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    d = np.asarray(dirs, dtype=np.float64)
+    ph = d[:, 0, None, None, None] * X[None] + d[:, 1, None, None, None] * Y[None] + d[:, 2, None, None, None] * Z[None]
+    return np.exp(1j * kb * ph)
+
+
 def point_sources(src: np.ndarray, n: int, delta: float, kb: float) -> np.ndarray:
     """[T, n, n] incident fields of point (line) sources, u_in,t(r) = g(|r - r_t|)."""
     pts = grid_points(n, delta, 2)
@@ -163,18 +172,24 @@ def point_sources(src: np.ndarray, n: int, delta: float, kb: float) -> np.ndarra
 
 
 class Problem:
-    """Tables of one geometry: ghat (padded spectrum), H, incident fields."""
+    """Tables of one geometry: ghat (padded spectrum), H, incident fields.
+
+    2D: ``angles`` are plane-wave angles; 3D (dim = 3): ``angles`` are unit
+    propagation directions [T, 3] and receivers are [M, 3]."""
 
     def __init__(self, n: int, delta: float, angles, rx, wavelength: float = 1.0,
-                 eps_b: float = 1.0, P: int | None = None, u_in=None):
-        self.n, self.delta = n, delta
+                 eps_b: float = 1.0, P: int | None = None, u_in=None, dim: int = 2):
+        self.n, self.delta, self.dim = n, delta, dim
         self.k, self.kb = wavenumbers(wavelength, eps_b)
         self.P = P if P is not None else 2 * n
-        self.ghat = green_spectrum(n, self.P, delta, self.k, self.kb)
+        self.ghat = green_spectrum(n, self.P, delta, self.k, self.kb, dim)
         self.rx = np.asarray(rx, dtype=np.float64)
         self.H = sensing_matrix(self.rx, n, delta, self.k, self.kb)
         if u_in is None:
-            u_in = plane_waves(np.asarray(angles), n, delta, self.kb)
+            if dim == 2:
+                u_in = plane_waves(np.asarray(angles), n, delta, self.kb)
+            else:
+                u_in = plane_waves_3d(np.asarray(angles), n, delta, self.kb)
         self.u_in = np.asarray(u_in, dtype=np.complex128)
         self.T = self.u_in.shape[0]
 

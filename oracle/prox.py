@@ -49,6 +49,52 @@ def grad2_adj(px, py):
     return out
 
 
+def grad3(x):
+    """Forward differences (D_x, D_y, D_z) of a [z, y, x] volume, zero at the last index."""
+    dx = np.zeros_like(x)
+    dy = np.zeros_like(x)
+    dz = np.zeros_like(x)
+    dx[:, :, :-1] = x[:, :, 1:] - x[:, :, :-1]
+    dy[:, :-1, :] = x[:, 1:, :] - x[:, :-1, :]
+    dz[:-1, :, :] = x[1:, :, :] - x[:-1, :, :]
+    return dx, dy, dz
+
+
+def grad3_adj(px, py, pz):
+    """D^T (p_x, p_y, p_z): the exact adjoint of ``grad3``."""
+    out = np.zeros_like(px)
+    out[:, :, :-1] -= px[:, :, :-1]
+    out[:, :, 1:] += px[:, :, :-1]
+    out[:, :-1, :] -= py[:, :-1, :]
+    out[:, 1:, :] += py[:, :-1, :]
+    out[:-1, :, :] -= pz[:-1, :, :]
+    out[1:, :, :] += pz[:-1, :, :]
+    return out
+
+
+def fgp3(z, lam, iters, lo=-np.inf, hi=np.inf):
+    """3D FGP (isotropic TV over d = 1..3, the sum of Eq. 8 taken over three
+    axes in 3D); dual step 1/(12 lam)."""
+    z = np.asarray(z, dtype=np.float64)
+    if lam <= 0:
+        return np.clip(z, lo, hi)
+    pold = [np.zeros_like(z) for _ in range(3)]
+    r = [np.zeros_like(z) for _ in range(3)]
+    t = 1.0
+    step = 1.0 / (12.0 * lam)
+    for _ in range(iters):
+        x = np.clip(z - lam * grad3_adj(*r), lo, hi)
+        d = grad3(x)
+        q = [r[i] + step * d[i] for i in range(3)]
+        nrm = np.maximum(1.0, np.sqrt(q[0] ** 2 + q[1] ** 2 + q[2] ** 2))
+        p = [qi / nrm for qi in q]
+        t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        beta = (t - 1.0) / t_new
+        r = [p[i] + beta * (p[i] - pold[i]) for i in range(3)]
+        pold, t = p, t_new
+    return np.clip(z - lam * grad3_adj(*pold), lo, hi)
+
+
 def tv_iso(x):
     """Isotropic TV: sum_n sqrt(sum_d [D_d x]_n^2) (first term of Eq. 8 without tau)."""
     dx, dy = grad2(x)
@@ -86,8 +132,9 @@ def fgp(z, lam, iters, lo=-np.inf, hi=np.inf, return_dual=False):
 def prox_R(z, lam, iters, box_re=(0.0, 2.0), box_im=None):
     """prox of gamma R at z (Eq. 9's outer prox); complex z takes separable Re / Im proxes."""
     z = np.asarray(z)
-    xr = fgp(z.real, lam, iters, *box_re)
+    fg = fgp3 if z.ndim == 3 else fgp
+    xr = fg(z.real, lam, iters, *box_re)
     if box_im is None:
         return xr.astype(np.complex128)
-    xi = fgp(z.imag, lam, iters, *box_im)
+    xi = fg(z.imag, lam, iters, *box_im)
     return xr + 1j * xi

@@ -122,17 +122,17 @@ def solve_dense(Amat, b):
 def solve_fields(prob, f, B, x0=None, tol=1e-10, adjoint=False, maxiter=20000):
     """Solve A u_t = B_t (or A^H u_t = B_t) for every transmitter t, one at a time.
 
-    Returns the [T, n, n] solutions, iteration counts and true residuals.
+    Returns the [T, *f.shape] solutions, iteration counts and true residuals.
     """
-    n = prob.n
+    shape = f.shape
     op = prob.AH if adjoint else prob.A
-    apply = lambda v: op(f, v.reshape(n, n)).ravel()
+    apply = lambda v: op(f, v.reshape(shape)).ravel()
     out = np.empty_like(np.asarray(B, dtype=np.complex128))
     its, res = [], []
     for t in range(B.shape[0]):
         g = None if x0 is None else x0[t].ravel()
         x, it, r = solve(apply, B[t].ravel(), g, tol, maxiter)
-        out[t] = x.reshape(n, n)
+        out[t] = x.reshape(shape)
         its.append(it)
         res.append(r)
     return out, np.array(its), np.array(res)

@@ -135,6 +135,25 @@ def circle_receivers(M: int, radius: float) -> np.ndarray:
     return np.stack([radius * np.cos(phi), radius * np.sin(phi)], axis=1)
 
 
+def hemisphere_directions(rings=(11.25, 33.75, 56.25, 78.75), per_ring=12) -> np.ndarray:
+    """[rings x per_ring, 3] unit propagation directions towards +z: polar angles
+    ``rings`` (degrees from +z), azimuths spaced 360/per_ring, odd rings offset by
+    half a step."""
+    out = []
+    for i, th in enumerate(np.radians(rings)):
+        off = (np.pi / per_ring) if i % 2 else 0.0
+        ph = off + 2.0 * np.pi * np.arange(per_ring) / per_ring
+        out.append(np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.full(per_ring, np.cos(th))], 1))
+    return np.concatenate(out)
+
+
+def planar_receivers(side: int, pitch: float, z: float) -> np.ndarray:
+    """[side^2, 3] receivers on a centred square grid in the plane z = const."""
+    c = (np.arange(side) - (side - 1) / 2.0) * pitch
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.full(side * side, z)], axis=1)
+
+
 def complex_noise(seed: int, shape) -> np.ndarray:
     """Unit-variance circular complex Gaussian draws (a + ib)/sqrt(2)."""
     cnt = int(np.prod(shape))
@@ -164,14 +183,25 @@ CONFIGS = {
     "c2": dict(dim=2, n=256, delta=1.0 / 8, T=64, M=256, rx_radius=24.0, shapes=10,
                contrast=(0.0, 1.0), imag=0.05, snr_db=40.0, outer=100, tau=1e-3,
                tv_iters=20, alpha=0.96, seed=1710),
+    # 3D scalar: 64^3 voxels at lambda/6 (FFT 128^3), 5 spheres with contrast
+    # in [0, 0.3], 48 plane waves over the upper hemisphere (4 polar rings x 12
+    # azimuths), 32 x 32 receivers at lambda/2 pitch in the plane z = 8 lambda.
+    "c3": dict(dim=3, n=64, delta=1.0 / 6, T=48, M=1024, rx_plane=8.0, shapes=5,
+               contrast=(0.0, 0.3), imag=0.0, snr_db=40.0, outer=50, tau=1e-3,
+               tv_iters=20, alpha=0.96, seed=1711),
 }
 
 
 def make_inputs(name: str, T: int | None = None):
-    """Phantom, transmitter angles and receivers of a named workload."""
+    """Phantom, transmitters (2D: angles; 3D: unit directions [T, 3]) and receivers of a named workload."""
     cfg = dict(CONFIGS[name])
     if T is not None:
         cfg["T"] = T
+    if cfg["dim"] == 3:
+        f = sphere_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
+        tx = hemisphere_directions()[: cfg["T"]]
+        rx = planar_receivers(32, 0.5, cfg["rx_plane"])
+        return cfg, f, tx, rx
     f = ellipse_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
     angles = plane_wave_angles(CONFIGS[name]["T"])[: cfg["T"]]
     rx = circle_receivers(cfg["M"], cfg["rx_radius"])
