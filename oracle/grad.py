@@ -58,15 +58,15 @@ def born_hessian_norm(prob, iters=30, seed_vec=None):
     (u = u_in) data term; the step size gamma = c / L is a reading (the paper
     tunes gamma by hand, Sec. IV).
     """
-    n = prob.n
-    x = np.ones((n, n)) if seed_vec is None else np.array(seed_vec, dtype=np.float64)
+    shape = prob.u_in.shape[1:]
+    x = np.ones(shape) if seed_vec is None else np.array(seed_vec, dtype=np.float64)
     x /= np.linalg.norm(x)
     lam = 0.0
     for _ in range(iters):
-        y = np.zeros((n, n))
+        y = np.zeros(shape)
         for t in range(prob.T):
             Zt = prob.H @ (prob.u_in[t] * x).ravel()
-            y += np.real(np.conj(prob.u_in[t]) * (np.conj(prob.H).T @ Zt).reshape(n, n))
+            y += np.real(np.conj(prob.u_in[t]) * (np.conj(prob.H).T @ Zt).reshape(shape))
         lam = float(np.linalg.norm(y))
         x = y / lam
     return lam

@@ -177,7 +177,9 @@ class Cisor:
     """One imaging geometry: tables and workspace on the current CUDA device."""
 
     def __init__(self, n=None, delta=None, tx_angles=None, rx_pos=None, wavelength=1.0, eps_b=1.0, complex_f=False,
-                 pad=0, stream=None, _handle=None):
+                 pad=0, stream=None, dim=2, _handle=None):
+        """2D: tx_angles [T] plane-wave angles, rx_pos [M, 2].  3D (dim=3):
+        tx_angles [T, 3] unit propagation directions, rx_pos [M, 3]."""
         lib = load()
         self._lib = lib
         self._owned = _handle is None
@@ -185,11 +187,13 @@ class Cisor:
             self._ctx = _handle
             self.stream = stream
             self.complex_f = bool(complex_f)
+            self.dim = int(dim)
             self._read_sizes()
             return
-        self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64)
-        self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, 2)
-        g = Geometry(2, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
+        self.dim = int(dim)
+        self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64).reshape((-1, 3) if self.dim == 3 else (-1,))
+        self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, self.dim)
+        g = Geometry(self.dim, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
                      self._ang.ctypes.data_as(POINTER(c_double)), len(self._rx),
                      self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad))
         self._ctx = c_void_p()
@@ -222,7 +226,7 @@ class Cisor:
 
     # ----- tables
     def green_spectrum(self, out):
-        return _check(self._lib.cisor_green_spectrum(self._ctx, ptr(out, self.P * self.P)))
+        return _check(self._lib.cisor_green_spectrum(self._ctx, ptr(out, self.P ** self.dim)))
 
     def sensing_matrix(self, out):
         return _check(self._lib.cisor_sensing_matrix(self._ctx, ptr(out, self.M * self.N)))
@@ -314,10 +318,11 @@ class Cisor:
 
 
 def _geometry(g, keep):
-    ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64)
-    rx = np.ascontiguousarray(g["rx_pos"], dtype=np.float64).reshape(-1, 2)
+    dim = int(g.get("dim", 2))
+    ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64).reshape((-1, 3) if dim == 3 else (-1,))
+    rx = np.ascontiguousarray(g["rx_pos"], dtype=np.float64).reshape(-1, dim)
     keep += [ang, rx]
-    return Geometry(2, int(g["n"]), float(g["delta"]), float(g.get("wavelength", 1.0)), float(g.get("eps_b", 1.0)),
+    return Geometry(dim, int(g["n"]), float(g["delta"]), float(g.get("wavelength", 1.0)), float(g.get("eps_b", 1.0)),
                     len(ang), ang.ctypes.data_as(POINTER(c_double)), len(rx), rx.ctypes.data_as(POINTER(c_double)),
                     1 if g.get("complex_f") else 0, int(g.get("pad", 0)))
 
@@ -338,7 +343,8 @@ class Batch:
         for i, g in enumerate(geoms):
             h = c_void_p()
             _check(lib.cisor_batch_context(self._b, i, ctypes.byref(h)))
-            self.problems.append(Cisor(_handle=h, stream=self.stream, complex_f=g.get("complex_f", False)))
+            self.problems.append(Cisor(_handle=h, stream=self.stream, complex_f=g.get("complex_f", False),
+                                       dim=g.get("dim", 2)))
 
     def close(self):
         if getattr(self, "_b", None):

@@ -192,11 +192,12 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     return CISOR_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (g->dim != 2) {
-    set_error("only dim = 2 is supported (got %d)", g->dim);
+  if (g->dim != 2 && g->dim != 3) {
+    set_error("dim must be 2 or 3 (got %d)", g->dim);
     return CISOR_ERR_INVALID_ARG;
   }
-  if (g->n < 8 || g->n > 256 || !(g->delta > 0) || !(g->wavelength > 0) || !(g->eps_b > 0) || g->T < 1 ||
+  const int nmax = g->dim == 3 ? 128 : 256, pmax = g->dim == 3 ? 256 : 512;
+  if (g->n < 8 || g->n > nmax || !(g->delta > 0) || !(g->wavelength > 0) || !(g->eps_b > 0) || g->T < 1 ||
       g->T > 1024 || g->M < 1 || !g->tx_angles || !g->rx_pos) {
     set_error("invalid geometry (n %d, T %d, M %d, delta %g, wavelength %g, eps_b %g)", g->n, g->T, g->M, g->delta,
               g->wavelength, g->eps_b);
@@ -207,8 +208,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     P = 64;
     while (P < 2 * g->n - 1) P *= 2;
   }
-  if ((P & (P - 1)) != 0 || P < 64 || P > 512 || P < 2 * g->n - 1) {
-    set_error("FFT side %d must be a power of two in [64, 512] and >= 2n - 1 = %d", P, 2 * g->n - 1);
+  if ((P & (P - 1)) != 0 || P < 64 || P > pmax || P < 2 * g->n - 1) {
+    set_error("FFT side %d must be a power of two in [64, %d] and >= 2n - 1 = %d", P, pmax, 2 * g->n - 1);
     return CISOR_ERR_INVALID_ARG;
   }
   cisor_ctx* c = new (std::nothrow) cisor_ctx();
@@ -216,25 +217,25 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     set_error("out of host memory");
     return CISOR_ERR_OOM;
   }
-  c->dim = 2;
+  c->dim = g->dim;
   c->n = g->n;
   c->P = P;
   c->T = g->T;
   c->M = g->M;
   c->complex_f = g->complex_f ? 1 : 0;
-  c->N = (long long)g->n * g->n;
+  c->N = (long long)g->n * g->n * (g->dim == 3 ? g->n : 1);
   c->delta = g->delta;
   c->wavelength = g->wavelength;
   c->eps_b = g->eps_b;
   c->k = 2.0 * 3.14159265358979323846 / g->wavelength;
   c->kb = c->k * sqrt(g->eps_b);
-  c->tx_angles.assign(g->tx_angles, g->tx_angles + g->T);
-  c->rx_pos.assign(g->rx_pos, g->rx_pos + 2 * g->M);
+  const int d = g->dim;
+  c->tx_angles.assign(g->tx_angles, g->tx_angles + (d == 3 ? 3 * g->T : g->T));
+  c->rx_pos.assign(g->rx_pos, g->rx_pos + (size_t)d * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
   c->cols_nt = 512;
-  const int RB = conv_rows_per_block(P);
-  c->nblk = (c->n + RB - 1) / RB;
+  conv_geometry(c);
   {
     const int tiles = ((c->M + 63) / 64) * ((c->T + 31) / 32);
     int ks = (2 * 152 + tiles - 1) / tiles;
@@ -261,18 +262,19 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   const size_t TN = (size_t)c->T * c->N * sizeof(float2);
   const size_t Nb = (size_t)c->N * sizeof(float2);
   const size_t TM = (size_t)c->T * c->M * sizeof(float2);
-  ALLOC(c->ghat, sizeof(float2) * P * P);
+  const size_t Pd = (size_t)P * P * (d == 3 ? P : 1);
+  ALLOC(c->ghat, sizeof(float2) * Pd);
   ALLOC(c->tw, sizeof(float2) * P);
   ALLOC(c->twst, sizeof(float2) * 2 * 512);
   ALLOC(c->H, (size_t)c->M * c->N * sizeof(float2));
   ALLOC(c->u_in, TN);
-  ALLOC(c->R, (size_t)c->T * c->n * P * sizeof(float2));
+  ALLOC(c->R, (size_t)c->T * c->rtstride * sizeof(float2));
   ALLOC(c->r, TN);
   ALLOC(c->rhat, TN);
   ALLOC(c->p, TN);
   ALLOC(c->v, TN);
   ALLOC(c->s, TN);
-  ALLOC(c->tv, TN > sizeof(float2) * P * P ? TN : sizeof(float2) * P * P);
+  ALLOC(c->tv, TN > sizeof(float2) * Pd ? TN : sizeof(float2) * Pd);
   ALLOC(c->b, TN);
   ALLOC(c->u, TN);
   ALLOC(c->vadj, TN);
@@ -294,9 +296,9 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->dsum, sizeof(double) * 4);
   ALLOC(c->sparams, sizeof(double) * 2);
   ALLOC(c->tv_z, sizeof(float) * 2 * c->N);
-  ALLOC(c->tv_r0, sizeof(float) * 4 * c->N);
-  ALLOC(c->tv_r1, sizeof(float) * 4 * c->N);
-  ALLOC(c->tv_p, sizeof(float) * 4 * c->N);
+  ALLOC(c->tv_r0, sizeof(float) * 2 * d * c->N);
+  ALLOC(c->tv_r1, sizeof(float) * 2 * d * c->N);
+  ALLOC(c->tv_p, sizeof(float) * 2 * d * c->N);
 #undef ALLOC
   {
     cudaError_t e = cudaMallocHost((void**)&c->h_active, sizeof(int) * c->T);
@@ -336,7 +338,7 @@ cisor_status cisor_green_spectrum(cisor_ctx* c, void* out) {
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  const long long PP = (long long)c->P * c->P;
+  const long long PP = (long long)c->P * c->P * (c->dim == 3 ? c->P : 1);
   scale_copy_kernel<<<(unsigned)((PP + 255) / 256), 256, 0, c->stream>>>(c->ghat, c->tv, PP, (float)PP);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;

@@ -1,12 +1,14 @@
 // Internal declarations shared by the translation units of libcisor.
 //
 // Device data layout (all row-major, x index fastest):
-//   fields      [T, n, n]   complex64 (float2), transmitter-major
-//   f           [n, n]      complex64
-//   R (scratch) [T, n, P]   complex64: the padded field after the row FFT,
-//               only the n non-zero rows of the P x P padded image are kept
-//   ghat        [P, P]      complex64: spectrum of the circulant embedding of
-//               G (Sec. II, Eq. 3), pre-scaled by 1/P^2 for the two inverse FFTs
+//   fields      [T, n, n] (2D) / [T, n, n, n] (3D)   complex64 (float2), transmitter-major
+//   f           [n, n] / [n, n, n]                   complex64
+//   R (scratch) [T, n, P] (2D): the padded field after the x FFT; only the n
+//               non-zero rows of the P x P padded image are kept.
+//               [T, n, P, P] (3D): z slabs of the padded field after the x
+//               and y FFTs; only the n non-zero z slabs are kept.
+//   ghat        [P^d]    complex64: spectrum of the circulant embedding of
+//               G (Sec. II, Eq. 3), pre-scaled by 1/P^d for the inverse FFTs
 //   H           [M, N]      complex64 (Eq. 2)
 #pragma once
 #include <cuda_runtime.h>
@@ -70,8 +72,11 @@ struct cisor_ctx {
   // geometry
   int dim, n, P, T, M, complex_f;
   long long N;
+  int nrows;              // x rows per field: n (2D), n^2 (3D)
+  long long rslab;        // R offset between z slabs (3D: P^2)
+  long long rtstride;     // R elements per transmitter
   double delta, wavelength, eps_b, k, kb;
-  std::vector<double> tx_angles, rx_pos;
+  std::vector<double> tx_angles, rx_pos;  // 2D: [T] angles, [M, 2]; 3D: [T, 3] directions, [M, 3]
   int device;
   cudaStream_t stream;  // internal non-blocking stream; ordered against the caller's via events
   cudaStream_t user_stream;
@@ -98,7 +103,7 @@ struct cisor_ctx {
   int* h_active;    // pinned [T]
   double* dsum;     // device scalar accumulators [4]
   double* h_dsum;   // pinned [4]
-  // TV workspace (2 components x N floats each plane)
+  // TV workspace (d dual components x N floats per plane, up to 2 planes)
   float *tv_z, *tv_r0, *tv_r1, *tv_p;
   // graphs of a chunk of BiCGSTAB iterations
   cudaGraphExec_t graph[2];
@@ -161,6 +166,10 @@ enum { EPI_MATVEC = 0, EPI_RESID = 1, EPI_CONV_ADD = 2 };
 cisor_status conv_pass(cisor_ctx* c, const ConvOp& op);
 cisor_status conv_init(int P);
 int conv_rows_per_block(int P);
+// Fills nrows, rslab, rtstride and nblk from dim, n, P.
+void conv_geometry(cisor_ctx* c);
+long long conv_scratch_elems(int dim, int n, int P);  // R elements per transmitter
+int conv_kernels_per_pass(int dim);
 
 // solver.cu
 cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float2* b, float2* x,

@@ -925,7 +925,7 @@ cisor_status cisor_fno_warm_start(cisor_fno* F, cisor_ctx* c, const void* f, voi
     set_error("cisor_fno_warm_start: NULL argument");
     return CISOR_ERR_INVALID_ARG;
   }
-  if (c->n != FN || c->T > F->max_batch) {
+  if (c->dim != 2 || c->n != FN || c->T > F->max_batch) {
     set_error("cisor_fno_warm_start: the network is for 128 x 128 grids and at most %d transmitters", F->max_batch);
     return CISOR_ERR_INVALID_ARG;
   }

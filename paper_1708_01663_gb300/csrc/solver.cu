@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(32) bicg_scalar_kernel(int mode, int nblk, con
 // Each CTA covers the RB rows of one transmitter that a row-pass CTA covers,
 // so its partial lands in the same slot layout; two complex values per
 // 16-byte access when the row length is even.
-__global__ void __launch_bounds__(256) bicg_update_kernel(int n, int RB, int nblk, const int* __restrict__ active,
+__global__ void __launch_bounds__(256) bicg_update_kernel(int n, int nrows, int RB, int nblk,
+                                                          const int* __restrict__ active,
                                                           const double* __restrict__ scal, float2* __restrict__ x,
                                                           const float2* __restrict__ p, const float2* __restrict__ s,
                                                           const float2* __restrict__ tv, float2* __restrict__ r,
@@ -143,9 +144,9 @@ __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int RB, int nbl
   if (!active[t]) return;
   const double2* sc = reinterpret_cast<const double2*>(scal) + (size_t)t * SC_STRIDE;
   const float2 alpha = z_to_c(sc[SC_ALPHA]), omega = z_to_c(sc[SC_OMEGA]);
-  const long long N = (long long)n * n;
+  const long long N = (long long)nrows * n;
   const int row0 = blockIdx.x * RB;
-  const int rows = min(RB, n - row0);
+  const int rows = min(RB, nrows - row0);
   const long long base = t * N + (long long)row0 * n;
   const int cnt = rows * n;
   float2 a0 = make_float2(0.f, 0.f);
@@ -277,7 +278,7 @@ static cisor_status enqueue_iteration(cisor_ctx* c, int adjoint, float2* x, int 
   CISOR_TRY(scalar_step(c, SCM_OMEGA, ntx));
   const int RB = conv_rows_per_block(c->P);
   dim3 g(c->nblk, ntx);
-  bicg_update_kernel<<<g, 256, 0, c->stream>>>(c->n, RB, c->nblk, c->active, c->scal, x, c->p, c->s, c->tv, c->r,
+  bicg_update_kernel<<<g, 256, 0, c->stream>>>(c->n, c->nrows, RB, c->nblk, c->active, c->scal, x, c->p, c->s, c->tv, c->r,
                                                c->rhat, c->part);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;

@@ -74,7 +74,9 @@ extern "C" cisor_status cisor_apply_A_static(const void* ghat_scaled, const void
   c.twst = reinterpret_cast<float2*>(base);
   c.R = reinterpret_cast<float2*>(base) + kStaticTwiddleFloats2;
   c.ghat = reinterpret_cast<float2*>(const_cast<void*>(ghat_scaled));
-  c.nblk = (n + conv_rows_per_block(P) - 1) / conv_rows_per_block(P);
+  c.dim = 2;
+  c.cols_nt = 512;
+  conv_geometry(&c);
   CISOR_TRY(make_stage_twiddles(&c));
   ConvOp op{};
   op.adjoint = adjoint ? 1 : 0;

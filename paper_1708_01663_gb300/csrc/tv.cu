@@ -13,24 +13,25 @@
 // takes the separable prox: Re and Im planes, each with its own box.
 // The last kernel also applies the relaxed-FISTA momentum of Eq. 11,
 // s_{k+1} = f_k + beta (f_k - f_{k-1}).
+// 3D volumes take the same iteration with p = (p_x, p_y, p_z), the unit-ball
+// projection in R^3 and the dual step 1 / (12 lam) (||D||^2 <= 4 d).
 #include <math.h>
 
 #include "common.cuh"
 
 namespace cisor {
 
+// Dual planes: component k of plane c at (dim * c + k) * N.
 __global__ void tv_split_kernel(const float2* __restrict__ z, float* __restrict__ zp, float* __restrict__ r,
-                                float* __restrict__ p, long long N, int ncomp) {
+                                float* __restrict__ p, long long N, int ncomp, int dim) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float2 v = z[i];
   zp[i] = v.x;
   if (ncomp == 2) zp[N + i] = v.y;
-  for (int c = 0; c < ncomp; ++c) {
-    r[2 * c * N + i] = 0.f;
-    r[(2 * c + 1) * N + i] = 0.f;
-    p[2 * c * N + i] = 0.f;
-    p[(2 * c + 1) * N + i] = 0.f;
+  for (int k = 0; k < dim * ncomp; ++k) {
+    r[k * N + i] = 0.f;
+    p[k * N + i] = 0.f;
   }
 }
 
@@ -80,18 +81,74 @@ __global__ void tv_iter_kernel(const float* __restrict__ zp, const float* __rest
   ro[N + i] = py + beta * (py - poy);
 }
 
-__global__ void tv_final_kernel(const float* __restrict__ zp, const float* __restrict__ p, int n, float lam, float lo0,
-                                float hi0, float lo1, float hi1, int ncomp, float2* x, const float2* fprev,
+// (D^T r) at voxel (iz, iy, ix) of an n^3 volume
+__device__ __forceinline__ float dt3_at(const float* __restrict__ rx, const float* __restrict__ ry,
+                                        const float* __restrict__ rz, int iz, int iy, int ix, int n) {
+  const long long nn = (long long)n * n;
+  const long long i = iz * nn + (long long)iy * n + ix;
+  float v = 0.f;
+  if (ix < n - 1) v -= rx[i];
+  if (ix > 0) v += rx[i - 1];
+  if (iy < n - 1) v -= ry[i];
+  if (iy > 0) v += ry[i - n];
+  if (iz < n - 1) v -= rz[i];
+  if (iz > 0) v += rz[i - nn];
+  return v;
+}
+
+__global__ void tv_iter3_kernel(const float* __restrict__ zp, const float* __restrict__ rin, float* __restrict__ rout,
+                                float* __restrict__ p, int n, float lam, float step, float beta, float lo0, float hi0,
+                                float lo1, float hi1) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y, iz = blockIdx.z % n, c = blockIdx.z / n;
+  const long long nn = (long long)n * n, N = nn * n;
+  const float lo = c ? lo1 : lo0, hi = c ? hi1 : hi0;
+  const float* z = zp + c * N;
+  const float* rx = rin + 3 * c * N;
+  const float* ry = rx + N;
+  const float* rz = ry + N;
+  const bool valid = ix < n;
+  const int xi = valid ? ix : n - 1;
+  const long long i = iz * nn + (long long)iy * n + xi;
+  auto xat = [&](int zz, int yy, int xx, long long j) {
+    return fminf(fmaxf(z[j] - lam * dt3_at(rx, ry, rz, zz, yy, xx, n), lo), hi);
+  };
+  const float x0 = xat(iz, iy, xi, i);
+  // right neighbour from the next lane; the last lane of a warp computes it itself
+  float xr = __shfl_down_sync(0xffffffffu, x0, 1);
+  const int lane = threadIdx.x & 31;
+  if (lane == 31 && xi < n - 1) xr = xat(iz, iy, xi + 1, i + 1);
+  if (!valid) return;
+  const float dx = (ix < n - 1) ? xr - x0 : 0.f;
+  const float dy = (iy < n - 1) ? xat(iz, iy + 1, ix, i + n) - x0 : 0.f;
+  const float dz = (iz < n - 1) ? xat(iz + 1, iy, ix, i + nn) - x0 : 0.f;
+  const float qx = rx[i] + step * dx, qy = ry[i] + step * dy, qz = rz[i] + step * dz;
+  const float nrm = fmaxf(1.f, sqrtf(qx * qx + qy * qy + qz * qz));
+  const float px = qx / nrm, py = qy / nrm, pz = qz / nrm;
+  float* pc = p + 3 * c * N;
+  const float pox = pc[i], poy = pc[N + i], poz = pc[2 * N + i];
+  pc[i] = px;
+  pc[N + i] = py;
+  pc[2 * N + i] = pz;
+  float* ro = rout + 3 * c * N;
+  ro[i] = px + beta * (px - pox);
+  ro[N + i] = py + beta * (py - poy);
+  ro[2 * N + i] = pz + beta * (pz - poz);
+}
+
+__global__ void tv_final_kernel(const float* __restrict__ zp, const float* __restrict__ p, int n, int dim, float lam,
+                                float lo0, float hi0, float lo1, float hi1, int ncomp, float2* x, const float2* fprev,
                                 float beta_mom, float2* __restrict__ s_out) {
-  const long long N = (long long)n * n;
+  const long long N = dim == 3 ? (long long)n * n * n : (long long)n * n;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int iy = (int)(i / n), ix = (int)(i % n);
+  const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
   float xv[2] = {0.f, 0.f};
   for (int c = 0; c < ncomp; ++c) {
     const float lo = c ? lo1 : lo0, hi = c ? hi1 : hi0;
-    const float* pc = p + 2 * c * N;
-    const float d = lam > 0.f ? dt_at(pc, pc + N, iy, ix, n) : 0.f;
+    const float* pc = p + dim * c * N;
+    float d = 0.f;
+    if (lam > 0.f) d = dim == 3 ? dt3_at(pc, pc + N, pc + 2 * N, iz, iy, ix, n) : dt_at(pc, pc + N, iy, ix, n);
     xv[c] = fminf(fmaxf(zp[c * N + i] - lam * d, lo), hi);
   }
   const float2 xo = make_float2(xv[0], xv[1]);
@@ -109,21 +166,26 @@ cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int i
   const long long N = c->N;
   const int ncomp = complex_f ? 2 : 1;
   const unsigned gN = (unsigned)((N + 255) / 256);
-  tv_split_kernel<<<gN, 256, 0, c->stream>>>(z, c->tv_z, c->tv_r0, c->tv_p, N, ncomp);
+  const int dim = c->dim;
+  tv_split_kernel<<<gN, 256, 0, c->stream>>>(z, c->tv_z, c->tv_r0, c->tv_p, N, ncomp, dim);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   if (lam > 0.0 && iters > 0) {
     const int bx = ((n + 31) / 32) * 32 > 256 ? 256 : ((n + 31) / 32) * 32;
-    dim3 g((n + bx - 1) / bx, n, ncomp);
+    dim3 g((n + bx - 1) / bx, n, dim == 3 ? n * ncomp : ncomp);
     double t = 1.0;
     float* rin = c->tv_r0;
     float* rout = c->tv_r1;
-    const float step = (float)(1.0 / (8.0 * lam));
+    const float step = (float)(1.0 / (4.0 * dim * lam));
     for (int k = 0; k < iters; ++k) {
       const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
       const float beta = (float)((t - 1.0) / tn);
-      tv_iter_kernel<<<g, bx, 0, c->stream>>>(c->tv_z, rin, rout, c->tv_p, n, (float)lam, step, beta, (float)lo,
-                                              (float)hi, (float)lo_im, (float)hi_im);
+      if (dim == 3)
+        tv_iter3_kernel<<<g, bx, 0, c->stream>>>(c->tv_z, rin, rout, c->tv_p, n, (float)lam, step, beta, (float)lo,
+                                                 (float)hi, (float)lo_im, (float)hi_im);
+      else
+        tv_iter_kernel<<<g, bx, 0, c->stream>>>(c->tv_z, rin, rout, c->tv_p, n, (float)lam, step, beta, (float)lo,
+                                                (float)hi, (float)lo_im, (float)hi_im);
       CISOR_CUDA(cudaGetLastError());
       c->launches += 1;
       float* tmp = rin;
@@ -133,7 +195,7 @@ cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int i
     }
   }
   const float lam_f = (lam > 0.0 && iters > 0) ? (float)lam : 0.f;
-  tv_final_kernel<<<gN, 256, 0, c->stream>>>(c->tv_z, c->tv_p, n, lam_f, (float)lo, (float)hi, (float)lo_im,
+  tv_final_kernel<<<gN, 256, 0, c->stream>>>(c->tv_z, c->tv_p, n, dim, lam_f, (float)lo, (float)hi, (float)lo_im,
                                              (float)hi_im, ncomp, x, f_prev, (float)beta_mom, s_out);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;

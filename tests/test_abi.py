@@ -26,7 +26,8 @@ def test_version_and_empty_error(lib):
 
 
 @pytest.mark.parametrize("kw", [dict(n=4), dict(n=300), dict(T=0), dict(delta=0.0), dict(pad=100),
-                                dict(pad=64, n=64), dict(dim=3)])
+                                dict(pad=64, n=64), dict(dim=4), dict(dim=1), dict(dim=3, n=200),
+                                dict(dim=3, pad=512)])
 def test_create_rejects_bad_geometry(lib, kw):
     ang = np.zeros(4)
     rx = np.ones((3, 2)) * 10
