@@ -10,6 +10,10 @@ a cold start to true relative residual 1e-4, sensing and adjoint sensing, the
 gradient (Prop. 1), the FGP TV prox and the momentum update.  The metric
 counts LS field solves (forward + adjoint) per second.
 
+``--config c3`` runs the 3D workload instead: 64^3 voxels at lambda/6 (FFT
+128^3), 48 plane waves over the upper hemisphere, 1024 receivers on a plane,
+5 seeded random spheres with contrast up to 0.3.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
 """
@@ -124,16 +128,41 @@ def _state0(f_true):
     return np.ascontiguousarray(s0, dtype=np.complex64)
 
 
-def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
-    """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds)."""
+# 3D oracle solves take minutes each: the sample is this many FP64 BiCGSTAB
+# iterations, counted as (iterations / mean iterations of a GPU solve) solves.
+ORACLE_3D_ITERS = 12
+ORACLE_3D_ITERS_PER_SOLVE = 250.0  # mean forward-solve iterations of the 3D workload, cold start, 1e-4
+
+
+def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol, iters_per_solve=None):
+    """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds, note).
+    3D: a fixed number of iterations of one solve, scaled to solves."""
     from oracle import model, solve
-    n = cfg["n"]
-    prob = model.Problem(n, cfg["delta"], angles[list(txs)], rx)
-    apply = lambda v: prob.A(f_point, v.reshape(n, n)).ravel()
+    n, dim = cfg["n"], cfg["dim"]
+    shape = (n,) * dim
+    tx = np.asarray(angles)[list(txs)]
+    prob = model.Problem(n, cfg["delta"], tx, rx, dim=dim)
+    apply = lambda v: prob.A(f_point, v.reshape(shape)).ravel()
     t0 = time.perf_counter()
+    if dim == 3:
+        solve.bicgstab(apply, prob.u_in[0].ravel(), prob.u_in[0].ravel(), 0.0, ORACLE_3D_ITERS)
+        sec = time.perf_counter() - t0
+        ips = iters_per_solve or ORACLE_3D_ITERS_PER_SOLVE
+        return ORACLE_3D_ITERS / ips, sec, (f"{ORACLE_3D_ITERS} FP64 BiCGSTAB iterations of transmitter {txs[0]} "
+                                           f"counted as {ORACLE_3D_ITERS}/{ips:.0f} of a solve, {sec:.1f} s")
     for t in range(len(txs)):
         solve.bicgstab(apply, prob.u_in[t].ravel(), prob.u_in[t].ravel(), tol, 20000)
-    return len(txs), time.perf_counter() - t0
+    sec = time.perf_counter() - t0
+    return len(txs), sec, (f"{len(txs)} cold-start forward solves (transmitters {txs[0]}-{txs[-1]}) to residual "
+                           f"{tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s")
+
+
+def _workload(name, cfg):
+    T, M = cfg["T"], cfg["M"]
+    if cfg["dim"] == 3:
+        return (f"{name}: 64^3 voxels at lambda/6, FFT 128^3, {T} plane waves over the upper hemisphere, "
+                f"{M} Rx on a plane, 5 spheres contrast<=0.3, 40 dB")
+    return f"{name}: 256x256 grid at lambda/8, FFT 512x512, {T} Tx, {M} Rx, 10 ellipses contrast<=1.0+0.05i, 40 dB"
 
 
 def run_reference(args):
@@ -143,22 +172,25 @@ def run_reference(args):
     from paper_1708_01663_gb300 import synth
     cfg, f_true, angles, rx = synth.make_inputs(args.config)
     s0 = _state0(f_true).astype(np.complex128)
-    times = []
+    times, solves = [], []
     for k in range(args.warmup + args.steps):
         t = k % cfg["T"]
-        nsolve, sec = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
+        nsolve, sec, note = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
         if k >= args.warmup:
             times.append(sec)
+            solves.append(nsolve)
     total = sum(times)
-    value = args.steps / total
+    value = sum(solves) / total
+    sample = ("one cold-start forward field solve per step (transmitter k mod T)" if cfg["dim"] == 2 else
+              f"{ORACLE_3D_ITERS} BiCGSTAB iterations of one transmitter per step, counted as "
+              f"{ORACLE_3D_ITERS}/{ORACLE_3D_ITERS_PER_SOLVE:.0f} of a solve")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.config}: 256x256 lambda/8, P=512, 64 Tx, 256 Rx, contrast<=1+0.05i",
-                   "sample": "one cold-start forward field solve per step (transmitter k mod 64)"},
+        "config": {"workload": _workload(args.config, cfg), "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 numpy BiCGSTAB, one transmitter per step, cold start to 1e-4"},
+                         "sample": "FP64 numpy BiCGSTAB, cold start to 1e-4: " + sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -173,9 +205,9 @@ def conv_sources_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_summary():
+def _traffic_summary(config):
     """ncu DRAM bytes per matvec pass from profiles/, valid only while the kernels are unchanged."""
-    path = os.path.join(ROOT, "profiles", "conv_matvec_c2.md")
+    path = os.path.join(ROOT, "profiles", f"conv_matvec_{config}.md")
     try:
         with open(path) as fh:
             text = fh.read()
@@ -209,9 +241,9 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     cfg, f_true, angles, rx = synth.make_inputs(args.config)
-    n, T, M = cfg["n"], cfg["T"], cfg["M"]
+    n, T, M, dim = cfg["n"], cfg["T"], cfg["M"], cfg["dim"]
     complex_f = cfg["imag"] != 0.0
-    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f)
+    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim)
     cols_nt = ctx.autotune(reps=10)  # pick the column-FFT CTA shape by measurement
 
     # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
@@ -222,10 +254,10 @@ def main():
     noise = torch.from_numpy(synth.complex_noise(cfg["seed"] + 100, (T, M)).astype(np.complex64)).to(dev)
     sigma = float(torch.linalg.vector_norm(y_dev)) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(T * M)
     y_dev += sigma * noise
-    Hh = np.empty((M, n * n), np.complex64)
-    ctx.sensing_matrix(Hh)
-    gamma = 1.0 / (T * float(np.sum(np.abs(Hh.astype(np.complex128)) ** 2)))  # L_Born <= T ||H||_F^2
-    del Hh
+    H_dev = torch.empty((M, ctx.N), dtype=torch.complex64, device=dev)
+    ctx.sensing_matrix(H_dev)
+    gamma = 1.0 / (T * float(torch.linalg.vector_norm(H_dev)) ** 2)  # L_Born <= T ||H||_F^2
+    del H_dev
 
     s0 = torch.from_numpy(_state0(f_true)).to(dev)
     f_st = torch.empty_like(s0)
@@ -304,23 +336,23 @@ def main():
     # roofline of the dominant kernel chain: one batched FFT matvec over all T transmitters,
     # timed with CUDA events on the library's own stream (cisor_time_matvec)
     mv_ms = ctx.time_matvec(s0, adjoint=False, reps=20)
-    N = n * n
-    P = ctx.P
+    N = ctx.N
+    Pd = ctx.P ** dim
     alg_bytes = T * 16 * N + 8 * N                       # read x, write y per transmitter, f once
-    alg_flops = T * 2 * 5 * P * P * np.log2(P * P)       # forward + inverse P^2 FFT per transmitter (unpruned)
+    alg_flops = T * 2 * 5 * Pd * np.log2(Pd)             # forward + inverse P^d FFT per transmitter (unpruned)
     achieved_tf = alg_flops / (mv_ms * 1e-3) / 1e12
     achieved_gbs = alg_bytes / (mv_ms * 1e-3) / 1e9
     hbm_peak, peak_kind = _peaks()
     fp32_peak = FP32_PEAK_TFLOPS
-    traffic = _traffic_summary()
+    traffic = _traffic_summary(args.config)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         s0n = _state0(f_true).astype(np.complex128)
-        nsolve, sec = _oracle_sample_solves(cfg, s0n, angles, rx, [0, 1], args.tol)
-        cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsolve} cold-start forward solves (transmitters 0-1 of {T}) to residual "
-                         f"{args.tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"}
+        ips = float(np.mean([i["iters_mean"] for i in step_infos])) if step_infos else None
+        nsolve, sec, note = _oracle_sample_solves(cfg, s0n, angles, rx, [0, 1] if dim == 2 else [0], args.tol,
+                                                  iters_per_solve=ips)
+        cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note}
 
     if rank == 0:
         it_f = [i["iters_mean"] for i in step_infos]
@@ -329,12 +361,11 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": f"{args.config}: 256x256 grid at lambda/8, FFT 512x512, {T} Tx, {M} Rx, "
-                                   "10 ellipses contrast<=1.0+0.05i, 40 dB",
+            "config": {"workload": _workload(args.config, cfg),
                        "step": "one relaxed-FISTA iteration from a fixed state: T forward + T adjoint "
                                "cold-start solves to residual 1e-4, sensing, gradient, FGP prox (20 it)",
                        "solves_per_step": solves_per_step, "start": "cold (u_in / 0)",
-                       "l2": "working set > L2 (Krylov vectors 12 x 32 MB)",
+                       "l2": f"working set > L2 (Krylov vectors 12 x {T * N * 8 / 2**20:.0f} MB)",
                        "parallelism": "independent replicas" if ws > 1 else "single GPU",
                        "autotuned_cols_cta": cols_nt,
                        "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
@@ -345,7 +376,9 @@ def main():
                        "not_converged": sum(i["n_not_converged"] for i in step_infos)},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / fp32_peak, "traffic": traffic,
-                         "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)",
+                         "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)"
+                                   if dim == 2 else "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols "
+                                   "y-forward + conv_cols z-spectrum + conv_cols y-inverse + conv_rows_inv)",
                          "ms_per_launch": mv_ms, "alg_flops_per_launch": alg_flops,
                          "alg_bytes_per_launch": alg_bytes,
                          "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 x 2.07 GHz",

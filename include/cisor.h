@@ -171,6 +171,17 @@ cisor_status cisor_tv_prox(cisor_ctx* ctx, const void* z, void* x, double gamma_
 cisor_status cisor_step(cisor_ctx* ctx, cisor_fista_state* st, const void* y, const cisor_solve_opts* opts,
                         cisor_solve_info* info);
 
+/* Update half of cisor_step, for a gradient summed outside this context:
+ * the transmitters split over several contexts (one per rank or GPU), each
+ * running cisor_grad on its own transmitters, and the partial g and D summed
+ * (D and g are sums over transmitters, Eq. 7 and Prop. 1).  From that sum:
+ *   f_k     = prox_{gamma R}(s_k - gamma grad)    (Eq. 9; real f steps with Re grad)
+ *   t_{k+1}, s_{k+1}                              (Eqs. 10-11)
+ * grad: [N] complex64, Prop. 1's g summed over ALL transmitters; D: D(s_k)
+ * summed likewise, stored in st->D.  State as in cisor_step.  Identical
+ * inputs give identical outputs on every rank, so no broadcast follows. */
+cisor_status cisor_step_update(cisor_ctx* ctx, cisor_fista_state* st, const void* grad, double D);
+
 /* Number of CUDA kernels this context has launched since creation (kernels
  * inside replayed CUDA graphs included).  *count is a host long long. */
 cisor_status cisor_launch_count(const cisor_ctx* ctx, long long* count);

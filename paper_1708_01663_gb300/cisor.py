@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "cisor_grad": [vp, vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_tv_prox": [vp, vp, vp, d, i, d, d, d, d],
         "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
+        "cisor_step_update": [vp, POINTER(FistaState), vp, c_double],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
@@ -315,6 +316,12 @@ class Cisor:
                                   ctypes.byref(info))
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return st, info
+
+
+    def step_update(self, state, grad, D):
+        """The prox and momentum half of step() from a gradient summed over all transmitters
+        (e.g. over the contexts of a transmitter split)."""
+        return _check(self._lib.cisor_step_update(self._ctx, ctypes.byref(state), ptr(grad, self.N), float(D)))
 
 
 def _geometry(g, keep):

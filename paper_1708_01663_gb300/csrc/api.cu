@@ -546,6 +546,50 @@ cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_ta
   return call.leave();
 }
 
+static bool state_ok(const cisor_ctx* c, const cisor_fista_state* st, const char* who) {
+  if (!(st->alpha >= 0.0 && st->alpha <= 1.0) || !(st->gamma > 0.0) || !(st->tau >= 0.0) || st->tv_iters < 0 ||
+      !(st->lo <= st->hi) || (c->complex_f && !(st->lo_im <= st->hi_im)) || !(st->t >= 1.0)) {
+    set_error("%s: invalid state (alpha %g, gamma %g, tau %g, t %g)", who, st->alpha, st->gamma, st->tau, st->t);
+    return false;
+  }
+  return true;
+}
+
+// f_k = prox(z) into work_n and s_{k+1} into c->f, from z in c->fz and f_{k-1} in work_n (Eqs. 9-11)
+static cisor_status prox_and_momentum(cisor_ctx* c, cisor_fista_state* st, double* tn_out) {
+  const double t = st->t;
+  const double tn = (sqrt(4.0 * t * t + 1.0) + 1.0) / 2.0;
+  const double beta = st->alpha * (t - 1.0) / tn;
+  CISOR_TRY(tv_prox(c, c->fz, c->work_n, st->gamma * st->tau, st->tv_iters, st->lo, st->hi, st->lo_im, st->hi_im,
+                    c->complex_f, c->work_n, beta, c->f));
+  *tn_out = tn;
+  return CISOR_OK;
+}
+
+cisor_status cisor_step_update(cisor_ctx* c, cisor_fista_state* st, const void* grad, double D) {
+  if (!c || !st || !st->f || !st->s || !grad) {
+    set_error("cisor_step_update: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!state_ok(c, st, "cisor_step_update")) return CISOR_ERR_INVALID_ARG;
+  Call call(c);
+  CISOR_TRY(call.enter());
+  const size_t nb = sizeof(float2) * c->N;
+  CISOR_TRY(call.in(c->f, st->s, nb));       // s_k
+  CISOR_TRY(call.in(c->work_n, st->f, nb));  // f_{k-1}
+  CISOR_TRY(call.in(c->grad, grad, nb));
+  CISOR_TRY(gradient_step(c, c->f, c->grad, st->gamma, c->fz));
+  double tn = 0.0;
+  CISOR_TRY(prox_and_momentum(c, st, &tn));
+  CISOR_TRY(call.out(st->f, c->work_n, nb));
+  CISOR_TRY(call.out(st->s, c->f, nb));
+  CISOR_TRY(call.leave());
+  st->t = tn;
+  st->k += 1;
+  st->D = D;
+  return CISOR_OK;
+}
+
 cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, const cisor_solve_opts* o,
                         cisor_solve_info* info) {
   if (!c || !st || !st->f || !st->s || !y) {
@@ -553,11 +597,7 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
     return CISOR_ERR_INVALID_ARG;
   }
   if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
-  if (!(st->alpha >= 0.0 && st->alpha <= 1.0) || !(st->gamma > 0.0) || !(st->tau >= 0.0) || st->tv_iters < 0 ||
-      !(st->lo <= st->hi) || (c->complex_f && !(st->lo_im <= st->hi_im)) || !(st->t >= 1.0)) {
-    set_error("cisor_step: invalid state (alpha %g, gamma %g, tau %g, t %g)", st->alpha, st->gamma, st->tau, st->t);
-    return CISOR_ERR_INVALID_ARG;
-  }
+  if (!state_ok(c, st, "cisor_step")) return CISOR_ERR_INVALID_ARG;
   Call call(c);
   CISOR_TRY(call.enter());
   const size_t nb = sizeof(float2) * c->N;
@@ -567,12 +607,8 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
   double D = 0.0;
   cisor_status s1 = grad_core(c, o, st->gamma, c->f, c->fz, &D, info);
   if (!solve_ok(s1)) return s1;
-  const double t = st->t;
-  const double tn = (sqrt(4.0 * t * t + 1.0) + 1.0) / 2.0;
-  const double beta = st->alpha * (t - 1.0) / tn;
-  // f_k = prox(s_k - gamma grad D(s_k)) into work_n, s_{k+1} into c->f
-  CISOR_TRY(tv_prox(c, c->fz, c->work_n, st->gamma * st->tau, st->tv_iters, st->lo, st->hi, st->lo_im, st->hi_im,
-                    c->complex_f, c->work_n, beta, c->f));
+  double tn = 0.0;
+  CISOR_TRY(prox_and_momentum(c, st, &tn));
   CISOR_TRY(call.out(st->f, c->work_n, nb));
   CISOR_TRY(call.out(st->s, c->f, nb));
   CISOR_TRY(call.leave());

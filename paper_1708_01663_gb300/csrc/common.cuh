@@ -199,6 +199,7 @@ cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, cons
 cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx);
 cisor_status grad_assemble(cisor_ctx* c, const float2* u, const float2* gz, const float2* s, double gamma,
                            float2* grad, float2* zstep, int ntx);
+cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, double gamma, float2* z);
 
 // tv.cu
 cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,

@@ -174,6 +174,23 @@ __global__ void __launch_bounds__(256) grad_kernel(const float2* __restrict__ u,
   }
 }
 
+// z = s - gamma g (real f: the real part of g only, Im z = 0): the gradient step of Eq. 9
+__global__ void __launch_bounds__(256) grad_step_kernel(const float2* __restrict__ s, const float2* __restrict__ g,
+                                                        long long N, float gamma, int complex_f,
+                                                        float2* __restrict__ z) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const float2 sv = s[n], gv = g[n];
+  z[n] = complex_f ? make_float2(sv.x - gamma * gv.x, sv.y - gamma * gv.y) : make_float2(sv.x - gamma * gv.x, 0.f);
+}
+
+cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, double gamma, float2* z) {
+  grad_step_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(s, g, c->N, (float)gamma, c->complex_f, z);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  return CISOR_OK;
+}
+
 cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Z, int ntx) {
   const long long chunk = ((c->N + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
   const int ks = (int)((c->N + chunk - 1) / chunk);

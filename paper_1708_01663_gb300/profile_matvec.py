@@ -2,11 +2,12 @@
 
     python -m paper_1708_01663_gb300.profile_matvec --config c2 --reps 3
 
-Builds the tables of a named workload (seeded phantom, all transmitters),
-autotunes the column-FFT tile and runs one untimed plus ``reps`` timed passes of y_t = A x_t over every
-transmitter through cisor_time_matvec.  Under ``ncu -k regex:conv -c 3`` the
-captured launches are the three kernels of the untimed pass; only the table
-set-up kernels run before them.
+Builds the tables of a named workload (seeded phantom, all transmitters, or
+the first ``--T``), autotunes the column-FFT tile (2 variants x (1 + 5)
+passes) and runs one untimed plus ``reps`` timed passes of y_t = A x_t over
+every transmitter through cisor_time_matvec.  A pass is k = 3 kernels in 2D
+and 5 in 3D, so ``ncu -k regex:conv_ -s 12k -c k`` captures the untimed pass
+that follows the autotuner (the column kernels in its chosen shape).
 """
 from __future__ import annotations
 
@@ -21,17 +22,18 @@ def main():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--T", type=int, default=None)
     args = ap.parse_args()
     import torch
 
     from paper_1708_01663_gb300 import build, cisor, synth
     build.build()
-    cfg, f, angles, rx = synth.make_inputs(args.config)
-    ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles, rx, complex_f=cfg["imag"] != 0.0)
+    cfg, f, angles, rx = synth.make_inputs(args.config, T=args.T)
+    ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles, rx, complex_f=cfg["imag"] != 0.0, dim=cfg["dim"])
     fd = torch.from_numpy(np.ascontiguousarray(0.9 * f, dtype=np.complex64)).cuda()
     cols = ctx.autotune(reps=5)  # column-FFT CTA size chosen by measurement
     ms = ctx.time_matvec(fd, adjoint=args.adjoint, reps=args.reps)
-    N = cfg["n"] ** 2
+    N = ctx.N
     alg = cfg["T"] * 16 * N + 8 * N
     print(json.dumps({"config": args.config, "T": cfg["T"], "n": cfg["n"], "P": ctx.P, "cols_cta": cols,
                       "ms_per_pass": ms,
