@@ -128,33 +128,47 @@ def _state0(f_true):
     return np.ascontiguousarray(s0, dtype=np.complex64)
 
 
-# 3D oracle solves take minutes each: the sample is this many FP64 BiCGSTAB
-# iterations, counted as (iterations / mean iterations of a GPU solve) solves.
-ORACLE_3D_ITERS = 12
-ORACLE_3D_ITERS_PER_SOLVE = 250.0  # mean forward-solve iterations of the 3D workload, cold start, 1e-4
-
-
-def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol, iters_per_solve=None):
-    """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds, note).
-    3D: a fixed number of iterations of one solve, scaled to solves."""
+def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
+    """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds, note, fields)."""
     from oracle import model, solve
     n, dim = cfg["n"], cfg["dim"]
     shape = (n,) * dim
-    tx = np.asarray(angles)[list(txs)]
-    prob = model.Problem(n, cfg["delta"], tx, rx, dim=dim)
+    prob = model.Problem(n, cfg["delta"], np.asarray(angles)[list(txs)], rx, dim=dim)
     apply = lambda v: prob.A(f_point, v.reshape(shape)).ravel()
     t0 = time.perf_counter()
-    if dim == 3:
-        solve.bicgstab(apply, prob.u_in[0].ravel(), prob.u_in[0].ravel(), 0.0, ORACLE_3D_ITERS)
-        sec = time.perf_counter() - t0
-        ips = iters_per_solve or ORACLE_3D_ITERS_PER_SOLVE
-        return ORACLE_3D_ITERS / ips, sec, (f"{ORACLE_3D_ITERS} FP64 BiCGSTAB iterations of transmitter {txs[0]} "
-                                           f"counted as {ORACLE_3D_ITERS}/{ips:.0f} of a solve, {sec:.1f} s")
-    for t in range(len(txs)):
-        solve.bicgstab(apply, prob.u_in[t].ravel(), prob.u_in[t].ravel(), tol, 20000)
+    xs = [solve.bicgstab(apply, prob.u_in[t].ravel(), prob.u_in[t].ravel(), tol, 20000)[0]
+          for t in range(len(txs))]
     sec = time.perf_counter() - t0
     return len(txs), sec, (f"{len(txs)} cold-start forward solves (transmitters {txs[0]}-{txs[-1]}) to residual "
-                           f"{tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s")
+                           f"{tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"), [x.reshape(shape) for x in xs]
+
+
+def _cufft_matvec_ms(ctx, f_dev, x_dev, dim, reps=20):
+    """Comparison only (never on the product path): the same batched A x with torch.fft (cuFFT):
+    zero-pad f x to P^d, FFT, times the library's own spectrum, inverse FFT, crop, subtract."""
+    import torch
+    P, n = ctx.P, ctx.n
+    gh = torch.empty((P,) * dim, dtype=torch.complex64, device=x_dev.device)
+    ctx.green_spectrum(gh)
+    axes = tuple(range(-dim, 0))
+    crop = (slice(None),) + (slice(0, n),) * dim
+    pad = torch.zeros((x_dev.shape[0],) + (P,) * dim, dtype=torch.complex64, device=x_dev.device)
+
+    def once():
+        pad[crop] = f_dev * x_dev
+        y = torch.fft.ifftn(torch.fft.fftn(pad, dim=axes) * gh, dim=axes)
+        return x_dev - y[crop]
+
+    for _ in range(3):
+        once()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def _workload(name, cfg):
@@ -175,15 +189,13 @@ def run_reference(args):
     times, solves = [], []
     for k in range(args.warmup + args.steps):
         t = k % cfg["T"]
-        nsolve, sec, note = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
+        nsolve, sec, note, _ = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
         if k >= args.warmup:
             times.append(sec)
             solves.append(nsolve)
     total = sum(times)
     value = sum(solves) / total
-    sample = ("one cold-start forward field solve per step (transmitter k mod T)" if cfg["dim"] == 2 else
-              f"{ORACLE_3D_ITERS} BiCGSTAB iterations of one transmitter per step, counted as "
-              f"{ORACLE_3D_ITERS}/{ORACLE_3D_ITERS_PER_SOLVE:.0f} of a solve")
+    sample = "one cold-start forward field solve per step (transmitter k mod T)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -265,6 +277,7 @@ def main():
     state = ctx.new_state(f_st, s_st, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0, 0.0, 0.5)
 
     infos = []
+    iters_all = []
 
     def step(st, y, f_buf, s_buf):
         f_buf.copy_(s0) if hasattr(f_buf, "copy_") else None
@@ -272,11 +285,13 @@ def main():
         st.t, st.k = 1.0, 1
         _, info = ctx.step(st, y, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
         infos.append(info.as_dict())
+        iters_all.extend(ctx.solve_iterations(False).tolist() + ctx.solve_iterations(True).tolist())
 
     for _ in range(args.warmup):
         step(state, y_dev, f_st, s_st)
     torch.cuda.synchronize()
     infos.clear()
+    iters_all.clear()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -345,14 +360,25 @@ def main():
     hbm_peak, peak_kind = _peaks()
     fp32_peak = FP32_PEAK_TFLOPS
     traffic = _traffic_summary(args.config)
+    u_in = torch.empty((T,) + (n,) * dim, dtype=torch.complex64, device=dev)
+    ctx.incident(u_in)
+    cufft_ms = _cufft_matvec_ms(ctx, s0, u_in, dim)
+    del u_in
 
     cpu = None
+    field_err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         s0n = _state0(f_true).astype(np.complex128)
-        ips = float(np.mean([i["iters_mean"] for i in step_infos])) if step_infos else None
-        nsolve, sec, note = _oracle_sample_solves(cfg, s0n, angles, rx, [0, 1] if dim == 2 else [0], args.tol,
-                                                  iters_per_solve=ips)
+        nsolve, sec, note, _ = _oracle_sample_solves(cfg, s0n, angles, rx, [0, 1], args.tol)
         cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note}
+        # error of the converged field (GPU, residual tol) against a tight FP64 oracle solve of transmitter 0
+        _, _, _, ref = _oracle_sample_solves(cfg, s0n, angles, rx, [0], 1e-9)
+        u_dev = torch.empty((T,) + (n,) * dim, dtype=torch.complex64, device=dev)
+        ctx.forward(s0, u_out=u_dev, tol=args.tol, max_iter=args.max_iter, check=False)
+        u0 = u_dev[0].cpu().numpy().astype(np.complex128)
+        field_err = {"rel_l2": float(np.linalg.norm(u0 - ref[0]) / np.linalg.norm(ref[0])),
+                     "what": f"transmitter 0 at the step's state, GPU solve to residual {args.tol:g} vs FP64 "
+                             "oracle solve to residual 1e-9"}
 
     if rank == 0:
         it_f = [i["iters_mean"] for i in step_infos]
@@ -373,7 +399,9 @@ def main():
                        "adj_iters_max": max(i["adj_iters_max"] for i in step_infos) if step_infos else None,
                        "adj_iters_mean": float(np.mean(it_a)) if it_a else None,
                        "resid_max": max(i["resid_max"] for i in step_infos) if step_infos else None,
-                       "not_converged": sum(i["n_not_converged"] for i in step_infos)},
+                       "not_converged": sum(i["n_not_converged"] for i in step_infos),
+                       "iters_p95": float(np.percentile(iters_all, 95)) if iters_all else None,
+                       "field_err_vs_oracle": field_err},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / fp32_peak, "traffic": traffic,
                          "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)"
@@ -384,6 +412,9 @@ def main():
                          "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 x 2.07 GHz",
                          "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth"}},
+            "comparison": {"cufft_matvec_ms": cufft_ms, "cisor_matvec_ms": mv_ms,
+                           "what": "the same batched A x over all T with torch.fft (cuFFT: pad, FFT, x ghat, IFFT, "
+                                   "crop) on the same inputs; timed for comparison only, not on the product path"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

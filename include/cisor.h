@@ -220,6 +220,16 @@ cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const 
  * Results do not depend on the choice. */
 cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
 
+/* Set the column-FFT CTA shape (512 or 256 threads) instead of measuring it;
+ * for reproducible profiles.  Drops the captured solver graphs. */
+cisor_status cisor_set_cols_cta(cisor_ctx* ctx, int cols_nt);
+
+/* Per-transmitter BiCGSTAB iterations of the last forward (adjoint = 0) or
+ * adjoint (adjoint = 1) solve on this context.  *count receives the number
+ * of transmitters of that solve (0 if none ran); iters_out (host [count],
+ * may be NULL to query the count) receives the iterations. */
+cisor_status cisor_solve_iterations(const cisor_ctx* ctx, int adjoint, int* iters_out, int* count);
+
 /* ---- Several problems of uneven size, solved together ----
  * A batch owns one context per geometry (grid side, transmitters and
  * receivers may all differ).  Its field solves advance every problem in ONE

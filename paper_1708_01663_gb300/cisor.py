@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
         "cisor_tv_prox": [vp, vp, vp, d, i, d, d, d, d],
         "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_step_update": [vp, POINTER(FistaState), vp, c_double],
+        "cisor_set_cols_cta": [vp, c_int],
+        "cisor_solve_iterations": [vp, c_int, POINTER(c_int), POINTER(c_int)],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
@@ -213,6 +215,18 @@ class Cisor:
         nt = c_int()
         _check(self._lib.cisor_autotune(self._ctx, int(reps), ctypes.byref(nt)))
         return nt.value
+
+    def set_cols_cta(self, nt):
+        return _check(self._lib.cisor_set_cols_cta(self._ctx, int(nt)))
+
+    def solve_iterations(self, adjoint=False):
+        """Per-transmitter iterations of the last forward (or adjoint) solve, as a numpy array."""
+        cnt = c_int()
+        _check(self._lib.cisor_solve_iterations(self._ctx, 1 if adjoint else 0, None, ctypes.byref(cnt)))
+        out = np.zeros(cnt.value, dtype=np.int32)
+        _check(self._lib.cisor_solve_iterations(self._ctx, 1 if adjoint else 0,
+                                                out.ctypes.data_as(POINTER(c_int)), ctypes.byref(cnt)))
+        return out
 
     def close(self):
         if getattr(self, "_ctx", None) and getattr(self, "_owned", True):

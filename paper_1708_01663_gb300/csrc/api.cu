@@ -618,6 +618,34 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
   return s1;
 }
 
+cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
+  if (!c || (cols_nt != 512 && cols_nt != 256)) {
+    set_error("cisor_set_cols_cta: NULL context or cols_nt not 512 / 256");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (cols_nt != c->cols_nt) {
+    c->cols_nt = cols_nt;
+    for (int i = 0; i < 2; ++i)  // captured graphs hold the previous kernel variant
+      if (c->graph[i]) {
+        CISOR_CUDA(cudaGraphExecDestroy(c->graph[i]));
+        c->graph[i] = nullptr;
+      }
+  }
+  return CISOR_OK;
+}
+
+cisor_status cisor_solve_iterations(const cisor_ctx* c, int adjoint, int* iters_out, int* count) {
+  if (!c || !count) {
+    set_error("cisor_solve_iterations: NULL argument");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  const std::vector<int>& it = c->last_iters[adjoint ? 1 : 0];
+  *count = (int)it.size();
+  if (iters_out)
+    for (size_t i = 0; i < it.size(); ++i) iters_out[i] = it[i];
+  return CISOR_OK;
+}
+
 cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   if (!c || reps < 1) {
     set_error("cisor_autotune: NULL context or reps < 1");

@@ -114,6 +114,7 @@ struct cisor_ctx {
   long long launches;       // kernels launched (graph replays add their kernel count)
   int cols_nt;              // threads per CTA of the column-FFT kernel (512 or 256), set by the autotuner
   long long graph_kernels[2];
+  std::vector<int> last_iters[2];  // per-transmitter iterations of the last forward / adjoint solve
 };
 
 namespace cisor {

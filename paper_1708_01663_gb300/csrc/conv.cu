@@ -30,7 +30,7 @@ namespace cisor {
 template <int P> struct ConvCfg {
   static constexpr int NTF = P / 8;         // threads per P-point transform
   static constexpr int RB = 256 / NTF;      // rows per CTA, row passes (256 threads)
-  static constexpr int PP = P + P / 16;     // padded row pitch in shared memory
+  static constexpr int PP = row_pitch(P);   // padded row pitch in shared memory
   template <int NT> struct Col { static constexpr int W = NT / NTF; };  // columns per CTA, column pass
 };
 
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
       }
       v[q * R0 + r] = val;
     }
-  reg_fft<P, false, false>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
+  reg_fft<P, false, false>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw);
   if (!rowok) return;
   constexpr int RL = PL::template last<false>();
   float2* dst = R + r_row<P>(geo, tx, iy);
@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
     for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += NT) twr[i] = tw_g[TW_STRIDE + i];
   float2* base = R + tx * geo.tstride + j * geo.slab + c0 + w;
   const ColLay<W> lay{w};
+  const ColLayRev<P, W> layr{w};
   float2 v[8];
   if (MODE == COL_INV) {
     constexpr int RI0 = PL::template first<true>();
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
         v[q * RL + r] = c_mul(v[q * RL + r], g);
       }
   }
-  reg_fft<P, true, true>(v, buf, lay, lay, lt, twr);
+  reg_fft<P, true, true>(v, buf, layr, layr, lt, twr);
   constexpr int RI = PL::template last<true>();
 #pragma unroll
   for (int q = 0; q < 8 / RI; ++q)
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
       pre_src[q * RL + r] = (ok && EPI != EPI_CONV_ADD) ? op.esrc[idx] : make_float2(0.f, 0.f);
       pre_aux[q * RL + r] = (ok && need_aux) ? op.aux[idx] : make_float2(0.f, 0.f);
     }
-  reg_fft<P, true, true>(v, buf, RowLayA{row * C::PP}, RowLayB{row * C::PP}, lt, tw);
+  reg_fft<P, true, true>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw);
   float2 acc[DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) acc[s] = make_float2(0.f, 0.f);

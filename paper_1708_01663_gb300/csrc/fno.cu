@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) fno_analysis(const float* __restrict__ v,
     float2 x[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) x[r] = make_float2(src[iy * FN + lt + 16 * r], 0.f);
-    reg_fft<FN, false, false>(x, xbuf, RowLayA{row * PP}, RowLayB{row * PP}, lt, tw);
+    reg_fft<FN, false, false>(x, xbuf, RowLayA<FN>{row * PP}, RowLayB<FN>{row * PP}, lt, tw);
     // output element lt (ky = lt) sits in x[0]
     colbuf[ColLay<FM>{lt}(iy)] = x[0];
   }
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) fno_synthesis(const float2* __restrict__ 
 #pragma unroll
     for (int r = 0; r < 8; ++r) x[r] = make_float2(0.f, 0.f);
     x[0] = colbuf[ColLay<FM>{lt}(iy)];                   // ky = lt (element lt, q = 0, r = 0)
-    reg_fft<FN, true, true>(x, xbuf, RowLayA{row * PP}, RowLayB{row * PP}, lt, tw);
+    reg_fft<FN, true, true>(x, xbuf, RowLayA<FN>{row * PP}, RowLayB<FN>{row * PP}, lt, tw);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       float* o = dst + iy * FN + lt + 16 * r;

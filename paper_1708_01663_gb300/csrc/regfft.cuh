@@ -37,21 +37,38 @@ template <int P> struct RPlan {
 
 // Shared-memory layouts, chosen so that the 16 threads of a half-warp (which
 // move 8-byte elements) hit 16 distinct bank pairs in every exchange pattern
-// of the plans above (checked by enumeration for P = 64..512):
-//  rows, first exchange : transform b at base b*(P + P/16), one pad slot every 16 elements;
-//  rows, second exchange: same region, bit 3 of the index flipped by bit 6;
-//  columns              : element i of column w at W*(i ^ ((i >> 3) & 3)) + w.
-struct RowLayA {
+// of the forward and the reversed plans above (checked by enumeration for
+// P = 64..512, both column-CTA shapes):
+//  rows, first exchange : transform b at base b * row_pitch(P); one pad slot
+//                         every 16 elements (P = 64, where a half-warp spans
+//                         two transforms: pitch 72 and i ^ ((i >> 3) & 7));
+//  rows, second exchange: bits 1-3 of the index flipped by bits 4-6 (P = 512:
+//                         bit 3 flipped by bit 6, equally conflict-free there);
+//  columns              : element i of column w at W * g(i) + w with
+//                         g(i) = i ^ ((i >> 3) & 3), except the reversed plan
+//                         of P = 256 at 8 columns per CTA: g(i) = i ^ ((i >> 2) & 1).
+__host__ __device__ constexpr int row_pitch(int P) { return P == 64 ? 72 : P + P / 16; }
+template <int P> struct RowLayA {
   int base;
-  __device__ __forceinline__ int operator()(int i) const { return base + i + (i >> 4); }
+  __device__ __forceinline__ int operator()(int i) const {
+    return P == 64 ? base + (i ^ ((i >> 3) & 7)) : base + i + (i >> 4);
+  }
 };
-struct RowLayB {
+template <int P> struct RowLayB {
   int base;
-  __device__ __forceinline__ int operator()(int i) const { return base + (i ^ (((i >> 6) & 1) << 3)); }
+  __device__ __forceinline__ int operator()(int i) const {
+    return P == 512 ? base + (i ^ (((i >> 6) & 1) << 3)) : base + (i ^ (((i >> 4) & 7) << 1));
+  }
 };
 template <int W> struct ColLay {
   int w;
   __device__ __forceinline__ int operator()(int i) const { return W * (i ^ ((i >> 3) & 3)) + w; }
+};
+template <int P, int W> struct ColLayRev {
+  int w;
+  __device__ __forceinline__ int operator()(int i) const {
+    return (P == 256 && W == 8) ? W * (i ^ ((i >> 2) & 1)) + w : W * (i ^ ((i >> 3) & 3)) + w;
+  }
 };
 
 // Twiddle table of one plan, stage by stage: stage s (s >= 1, sub-transform

@@ -348,14 +348,15 @@ static cisor_status true_residual(cisor_ctx* c, int adjoint, const float2* b, fl
 
 // Per-transmitter statistics of the last solve; the status reports any
 // transmitter above tol (breakdown or iteration cap).
-static cisor_status collect_stats(cisor_ctx* c, int ntx, double tol, int* iters_max, double* iters_mean,
-                                  double* resid_max, int* n_bad) {
+static cisor_status collect_stats(cisor_ctx* c, int adjoint, int ntx, double tol, int* iters_max,
+                                  double* iters_mean, double* resid_max, int* n_bad) {
   std::vector<int> it(ntx), fl(ntx);
   std::vector<double> sc((size_t)ntx * SC_STRIDE * 2);
   CISOR_CUDA(cudaMemcpyAsync(it.data(), c->iters, sizeof(int) * ntx, cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaMemcpyAsync(fl.data(), c->txflag, sizeof(int) * ntx, cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaMemcpyAsync(sc.data(), c->scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  c->last_iters[adjoint ? 1 : 0] = it;
   int imax = 0, bad = 0;
   double isum = 0.0, rmax = 0.0;
   for (int t = 0; t < ntx; ++t) {
@@ -398,7 +399,7 @@ cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float
     CISOR_TRY(true_residual(c, adjoint, b, x, ntx));
     CISOR_TRY(read_active(c, ntx, &nact));
   }
-  return collect_stats(c, ntx, tol, iters_max, iters_mean, resid_max, n_bad);
+  return collect_stats(c, adjoint, ntx, tol, iters_max, iters_mean, resid_max, n_bad);
 }
 
 // ---------------------------------------------------------------- several problems in one graph
@@ -468,7 +469,7 @@ cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2
   }
   cisor_status worst = CISOR_OK;
   for (int i = 0; i < np; ++i) {
-    st[i].status = collect_stats(cs[i], cs[i]->T, tol, &st[i].iters_max, &st[i].iters_mean, &st[i].resid_max,
+    st[i].status = collect_stats(cs[i], adjoint, cs[i]->T, tol, &st[i].iters_max, &st[i].iters_mean, &st[i].resid_max,
                                  &st[i].n_bad);
     if (st[i].status == CISOR_ERR_CUDA || st[i].status == CISOR_ERR_OOM) return st[i].status;
     if (st[i].status != CISOR_OK) worst = st[i].status;

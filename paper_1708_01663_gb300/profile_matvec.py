@@ -5,9 +5,10 @@
 Builds the tables of a named workload (seeded phantom, all transmitters, or
 the first ``--T``), autotunes the column-FFT tile (2 variants x (1 + 5)
 passes) and runs one untimed plus ``reps`` timed passes of y_t = A x_t over
-every transmitter through cisor_time_matvec.  A pass is k = 3 kernels in 2D
-and 5 in 3D, so ``ncu -k regex:conv_ -s 12k -c k`` captures the untimed pass
-that follows the autotuner (the column kernels in its chosen shape).
+every transmitter through cisor_time_matvec.  ``--cols-cta 512|256`` sets
+the column-kernel shape instead of measuring it, so that no convolution runs
+before the untimed pass and ``ncu -k regex:conv_ -c k`` (k = 3 kernels per
+pass in 2D, 5 in 3D) captures exactly that pass.
 """
 from __future__ import annotations
 
@@ -23,6 +24,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--T", type=int, default=None)
+    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 256, 512])
     args = ap.parse_args()
     import torch
 
@@ -31,7 +33,11 @@ def main():
     cfg, f, angles, rx = synth.make_inputs(args.config, T=args.T)
     ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles, rx, complex_f=cfg["imag"] != 0.0, dim=cfg["dim"])
     fd = torch.from_numpy(np.ascontiguousarray(0.9 * f, dtype=np.complex64)).cuda()
-    cols = ctx.autotune(reps=5)  # column-FFT CTA size chosen by measurement
+    if args.cols_cta:
+        ctx.set_cols_cta(args.cols_cta)
+        cols = args.cols_cta
+    else:
+        cols = ctx.autotune(reps=5)  # column-FFT CTA size chosen by measurement
     ms = ctx.time_matvec(fd, adjoint=args.adjoint, reps=args.reps)
     N = ctx.N
     alg = cfg["T"] * 16 * N + 8 * N
