@@ -12,7 +12,9 @@ counts LS field solves (forward + adjoint) per second.
 
 ``--config c3`` runs the 3D workload instead: 64^3 voxels at lambda/6 (FFT
 128^3), 48 plane waves over the upper hemisphere, 1024 receivers on a plane,
-5 seeded random spheres with contrast up to 0.3.
+5 seeded random spheres with contrast up to 0.3.  ``--config c6`` runs a
+Fresnel-style 2D set-up: 8 line sources, 360 receivers of which each source
+records the 240 farther than 60 degrees from it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -133,7 +135,8 @@ def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
     from oracle import model, solve
     n, dim = cfg["n"], cfg["dim"]
     shape = (n,) * dim
-    prob = model.Problem(n, cfg["delta"], np.asarray(angles)[list(txs)], rx, dim=dim)
+    prob = model.Problem(n, cfg["delta"], np.asarray(angles)[list(txs)], rx, dim=dim,
+                         tx_kind=cfg.get("tx_kind", "plane"))
     apply = lambda v: prob.A(f_point, v.reshape(shape)).ravel()
     t0 = time.perf_counter()
     xs = [solve.bicgstab(apply, prob.u_in[t].ravel(), prob.u_in[t].ravel(), tol, 20000)[0]
@@ -173,6 +176,10 @@ def _cufft_matvec_ms(ctx, f_dev, x_dev, dim, reps=20):
 
 def _workload(name, cfg):
     T, M = cfg["T"], cfg["M"]
+    if cfg.get("tx_kind") == "point":
+        return (f"{name}: Fresnel-style 2D, 128x128 over 1.5 lambda, FFT 256x256, {T} line sources at "
+                f"{cfg['tx_radius']} lambda, {M} Rx at {cfg['rx_radius']} lambda, receivers within "
+                f"{cfg['rx_min_deg']:.0f} deg of the source masked off, 3 ellipses contrast<=1.0, 40 dB")
     if cfg["dim"] == 3:
         return (f"{name}: 64^3 voxels at lambda/6, FFT 128^3, {T} plane waves over the upper hemisphere, "
                 f"{M} Rx on a plane, 5 spheres contrast<=0.3, 40 dB")
@@ -255,7 +262,9 @@ def main():
     cfg, f_true, angles, rx = synth.make_inputs(args.config)
     n, T, M, dim = cfg["n"], cfg["T"], cfg["M"], cfg["dim"]
     complex_f = cfg["imag"] != 0.0
-    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim)
+    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim, tx_kind=cfg.get("tx_kind", 0))
+    if "rx_mask" in cfg:
+        ctx.set_rx_mask(cfg["rx_mask"])
     cols_nt = ctx.autotune(reps=10)  # pick the column-FFT CTA shape by measurement
 
     # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
@@ -268,8 +277,11 @@ def main():
     y_dev += sigma * noise
     H_dev = torch.empty((M, ctx.N), dtype=torch.complex64, device=dev)
     ctx.sensing_matrix(H_dev)
-    gamma = 1.0 / (T * float(torch.linalg.vector_norm(H_dev)) ** 2)  # L_Born <= T ||H||_F^2
-    del H_dev
+    u_in = torch.empty((T, ctx.N), dtype=torch.complex64, device=dev)
+    ctx.incident(u_in)
+    # L_Born <= T max|u_in|^2 ||H||_F^2 (max |u_in| = 1 for plane waves)
+    gamma = 1.0 / (T * float(u_in.abs().max()) ** 2 * float(torch.linalg.vector_norm(H_dev)) ** 2)
+    del H_dev, u_in
 
     s0 = torch.from_numpy(_state0(f_true)).to(dev)
     f_st = torch.empty_like(s0)

@@ -45,20 +45,24 @@ typedef struct cisor_ctx cisor_ctx;
 
 /* Geometry of one imaging set-up (Sec. II and Appendix A, grid).
  * Pixel l = 1..n of each axis sits at (l - n/2 - 0.5) * delta.  Transmitters
- * are plane waves exp(j k_b (cos a_t x + sin a_t y)); receivers are points
- * outside the grid. */
+ * are plane waves exp(j k_b d_t . r) (d_t = (cos a_t, sin a_t) in 2D, a unit
+ * vector in 3D) or, with tx_kind = 1, unit point (3D) / line (2D) sources at
+ * positions outside the grid, u_in,t(r) = g(|r - r_t|) with g of Eq. 1 (the
+ * Fresnel set-ups of Sec. IV).  Receivers are points outside the grid. */
 typedef struct {
-  int dim;                  /* 2 (the scalar 2D model) */
-  int n;                    /* grid side, 8 <= n <= 256; N = n*n pixels */
+  int dim;                  /* 2 or 3 (the scalar models of Eq. 1) */
+  int n;                    /* grid side, 8 <= n <= 256 (2D) or 128 (3D); N = n^dim */
   double delta;             /* pixel size */
   double wavelength;        /* vacuum wavelength; k = 2 pi / wavelength */
   double eps_b;             /* background permittivity; k_b = k sqrt(eps_b) */
   int T;                    /* transmitters, 1 <= T <= 1024 */
-  const double* tx_angles;  /* host [T] plane-wave propagation angles, radians */
+  const double* tx_angles;  /* host; tx_kind 0: [T] angles, radians (2D) or [T, 3] unit directions (3D);
+                               tx_kind 1: [T, dim] source positions, each outside the grid's bounding box */
   int M;                    /* receivers, 1 <= M */
-  const double* rx_pos;     /* host [M, 2] receiver positions (x, y) */
+  const double* rx_pos;     /* host [M, dim] receiver positions */
   int complex_f;            /* 0: f real (Im f is neither updated nor regularised); 1: complex f */
-  int pad;                  /* FFT side P >= 2n - 1, a power of two <= 512; 0 = smallest such */
+  int pad;                  /* FFT side P >= 2n - 1, a power of two <= 512 (2D) / 256 (3D); 0 = smallest such */
+  int tx_kind;              /* 0: plane waves; 1: point / line sources */
 } cisor_geometry;
 
 /* Options of the field solves A u = u_in and A^H v = b (Eq. 13). */
@@ -219,6 +223,13 @@ cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const 
  * the faster.  *cols_nt_out (may be NULL) receives the chosen CTA size.
  * Results do not depend on the choice. */
 cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
+
+/* Per-transmitter receiver mask (the Fresnel set-ups of Sec. IV record each
+ * transmitter on a subset of the receivers): mask [T, M] bytes, non-zero =
+ * active, host or device, copied into the context.  D (Eq. 7) and the
+ * gradient (Prop. 1) then sum only active (t, m) pairs; inactive entries of y
+ * are ignored.  mask = NULL restores all receivers. */
+cisor_status cisor_set_rx_mask(cisor_ctx* ctx, const void* mask);
 
 /* Set the column-FFT CTA shape (512 or 256 threads) instead of measuring it;
  * for reproducible profiles.  Drops the captured solver graphs. */

@@ -11,8 +11,14 @@ grad D = Re g for real f (Eq. 12).  For complex f (absorbing objects, outside
 the paper's real-f assumption) the reading is: (Re f, Im f) are independent
 real unknowns, dD/dRe f = Re g, dD/dIm f = Im g, with A^H = I - diag(conj f) G^H.
 
+Receiver masks (a transmitter records only some receivers, as in the Fresnel
+experiments of Sec. IV): with mask[t, m] in {0, 1}, w_t = mask_t (Z_t - y_t), so
+D and g only see active receivers.
+
 Pinned by: central finite differences of D, the Taylor-remainder slope, the
-f = 0 special case, and brute-force dense solves (tests/test_oracle_grad.py).
+f = 0 special case, and brute-force dense solves (tests/test_oracle_grad.py);
+masks by per-transmitter sub-problems holding only the active receivers
+(tests/test_oracle_fresnel.py).
 """
 from __future__ import annotations
 
@@ -28,11 +34,13 @@ def forward(prob, f, tol=1e-10, x0=None):
     return u, prob.sense(f, u), its, res
 
 
-def data_and_grad(prob, f, y, tol=1e-10, u0=None, v0=None, return_fields=False):
+def data_and_grad(prob, f, y, tol=1e-10, u0=None, v0=None, return_fields=False, mask=None):
     """D(f) and the complex vector g of Prop. 1 (grad D = Re g for real f)."""
     n = prob.n
     u, Z, _, _ = forward(prob, f, tol, x0=u0)
     w = Z - y
+    if mask is not None:
+        w = w * np.asarray(mask, dtype=np.float64)
     D = 0.5 * float(np.sum(np.abs(w) ** 2))
     z = (w @ np.conj(prob.H)).reshape((-1,) + f.shape)  # H^H w_t for each t
     b = np.conj(f)[None] * z
@@ -45,10 +53,11 @@ def data_and_grad(prob, f, y, tol=1e-10, u0=None, v0=None, return_fields=False):
     return D, g
 
 
-def data_term(prob, f, y, tol=1e-12):
-    """D(f) = 1/2 sum_t ||y_t - Z_t(f)||^2 (Eq. 7)."""
+def data_term(prob, f, y, tol=1e-12, mask=None):
+    """D(f) = 1/2 sum_t ||y_t - Z_t(f)||^2 (Eq. 7), over active receivers if masked."""
     _, Z, _, _ = forward(prob, f, tol)
-    return 0.5 * float(np.sum(np.abs(Z - y) ** 2))
+    w = Z - y if mask is None else (Z - y) * np.asarray(mask, dtype=np.float64)
+    return 0.5 * float(np.sum(np.abs(w) ** 2))
 
 
 def born_hessian_norm(prob, iters=30, seed_vec=None):

@@ -165,26 +165,33 @@ def plane_waves_3d(dirs: np.ndarray, n: int, delta: float, kb: float) -> np.ndar
 
 
 def point_sources(src: np.ndarray, n: int, delta: float, kb: float) -> np.ndarray:
-    """[T, n, n] incident fields of point (line) sources, u_in,t(r) = g(|r - r_t|)."""
-    pts = grid_points(n, delta, 2)
+    """[T, n, n(, n)] incident fields of point (3D) or line (2D) sources at src [T, d]:
+    u_in,t(r) = g(|r - r_t|), Eq. 1's Green's function without the k^2 delta^d
+    quadrature weight (the field radiated by a unit source)."""
+    src = np.asarray(src, dtype=np.float64)
+    dim = src.shape[1]
+    pts = grid_points(n, delta, dim)
     d = np.sqrt(((src[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
-    return green(d, kb, 2).reshape(len(src), n, n)
+    return green(d, kb, dim).reshape((len(src),) + (n,) * dim)
 
 
 class Problem:
     """Tables of one geometry: ghat (padded spectrum), H, incident fields.
 
     2D: ``angles`` are plane-wave angles; 3D (dim = 3): ``angles`` are unit
-    propagation directions [T, 3] and receivers are [M, 3]."""
+    propagation directions [T, 3] and receivers are [M, 3].  With
+    tx_kind = "point", ``angles`` are source positions [T, d] instead."""
 
     def __init__(self, n: int, delta: float, angles, rx, wavelength: float = 1.0,
-                 eps_b: float = 1.0, P: int | None = None, u_in=None, dim: int = 2):
+                 eps_b: float = 1.0, P: int | None = None, u_in=None, dim: int = 2, tx_kind: str = "plane"):
         self.n, self.delta, self.dim = n, delta, dim
         self.k, self.kb = wavenumbers(wavelength, eps_b)
         self.P = P if P is not None else 2 * n
         self.ghat = green_spectrum(n, self.P, delta, self.k, self.kb, dim)
         self.rx = np.asarray(rx, dtype=np.float64)
         self.H = sensing_matrix(self.rx, n, delta, self.k, self.kb)
+        if u_in is None and tx_kind == "point":
+            u_in = point_sources(np.asarray(angles), n, delta, self.kb)
         if u_in is None:
             if dim == 2:
                 u_in = plane_waves(np.asarray(angles), n, delta, self.kb)

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "BREAKDOWN", 4
 class Geometry(Structure):
     _fields_ = [("dim", c_int), ("n", c_int), ("delta", c_double), ("wavelength", c_double),
                 ("eps_b", c_double), ("T", c_int), ("tx_angles", POINTER(c_double)), ("M", c_int),
-                ("rx_pos", POINTER(c_double)), ("complex_f", c_int), ("pad", c_int)]
+                ("rx_pos", POINTER(c_double)), ("complex_f", c_int), ("pad", c_int), ("tx_kind", c_int)]
 
 
 class SolveOpts(Structure):
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_step_update": [vp, POINTER(FistaState), vp, c_double],
         "cisor_set_cols_cta": [vp, c_int],
+        "cisor_set_rx_mask": [vp, vp],
         "cisor_solve_iterations": [vp, c_int, POINTER(c_int), POINTER(c_int)],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
@@ -180,9 +181,10 @@ class Cisor:
     """One imaging geometry: tables and workspace on the current CUDA device."""
 
     def __init__(self, n=None, delta=None, tx_angles=None, rx_pos=None, wavelength=1.0, eps_b=1.0, complex_f=False,
-                 pad=0, stream=None, dim=2, _handle=None):
+                 pad=0, stream=None, dim=2, tx_kind=0, _handle=None):
         """2D: tx_angles [T] plane-wave angles, rx_pos [M, 2].  3D (dim=3):
-        tx_angles [T, 3] unit propagation directions, rx_pos [M, 3]."""
+        tx_angles [T, 3] unit propagation directions, rx_pos [M, 3].
+        tx_kind=1 (or "point"): tx_angles holds source positions [T, dim]."""
         lib = load()
         self._lib = lib
         self._owned = _handle is None
@@ -194,11 +196,13 @@ class Cisor:
             self._read_sizes()
             return
         self.dim = int(dim)
-        self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64).reshape((-1, 3) if self.dim == 3 else (-1,))
+        kind = 1 if tx_kind in (1, "point") else 0
+        per_tx = (self.dim,) if kind == 1 else ((3,) if self.dim == 3 else ())
+        self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64).reshape((-1,) + per_tx)
         self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, self.dim)
         g = Geometry(self.dim, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
                      self._ang.ctypes.data_as(POINTER(c_double)), len(self._rx),
-                     self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad))
+                     self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad), kind)
         self._ctx = c_void_p()
         self.stream = _current_stream() if stream is None else stream
         _check(lib.cisor_create(ctypes.byref(self._ctx), ctypes.byref(g), self.stream))
@@ -215,6 +219,15 @@ class Cisor:
         nt = c_int()
         _check(self._lib.cisor_autotune(self._ctx, int(reps), ctypes.byref(nt)))
         return nt.value
+
+    def set_rx_mask(self, mask):
+        """Per-transmitter active receivers, [T, M] (non-zero = active); None restores all."""
+        if mask is None:
+            return _check(self._lib.cisor_set_rx_mask(self._ctx, None))
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        assert m.shape == (self.T, self.M)
+        self._mask = m
+        return _check(self._lib.cisor_set_rx_mask(self._ctx, m.ctypes.data_as(c_void_p)))
 
     def set_cols_cta(self, nt):
         return _check(self._lib.cisor_set_cols_cta(self._ctx, int(nt)))
@@ -340,12 +353,14 @@ class Cisor:
 
 def _geometry(g, keep):
     dim = int(g.get("dim", 2))
-    ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64).reshape((-1, 3) if dim == 3 else (-1,))
+    kind = 1 if g.get("tx_kind", 0) in (1, "point") else 0
+    per_tx = (dim,) if kind == 1 else ((3,) if dim == 3 else ())
+    ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64).reshape((-1,) + per_tx)
     rx = np.ascontiguousarray(g["rx_pos"], dtype=np.float64).reshape(-1, dim)
     keep += [ang, rx]
     return Geometry(dim, int(g["n"]), float(g["delta"]), float(g.get("wavelength", 1.0)), float(g.get("eps_b", 1.0)),
                     len(ang), ang.ctypes.data_as(POINTER(c_double)), len(rx), rx.ctypes.data_as(POINTER(c_double)),
-                    1 if g.get("complex_f") else 0, int(g.get("pad", 0)))
+                    1 if g.get("complex_f") else 0, int(g.get("pad", 0)), kind)
 
 
 class Batch:

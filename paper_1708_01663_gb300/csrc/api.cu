@@ -165,7 +165,7 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -203,6 +203,21 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
               g->wavelength, g->eps_b);
     return CISOR_ERR_INVALID_ARG;
   }
+  if (g->tx_kind != 0 && g->tx_kind != 1) {
+    set_error("tx_kind must be 0 (plane waves) or 1 (point sources), got %d", g->tx_kind);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (g->tx_kind == 1) {  // sources outside the grid's bounding box: g is never evaluated at r = 0
+    const double half = 0.5 * g->n * g->delta;
+    for (int t = 0; t < g->T; ++t) {
+      bool outside = false;
+      for (int a = 0; a < g->dim; ++a) outside |= fabs(g->tx_angles[(size_t)g->dim * t + a]) > half;
+      if (!outside) {
+        set_error("point source %d lies inside the grid's bounding box (half-width %g)", t, half);
+        return CISOR_ERR_INVALID_ARG;
+      }
+    }
+  }
   int P = g->pad;
   if (P == 0) {
     P = 64;
@@ -230,7 +245,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->k = 2.0 * 3.14159265358979323846 / g->wavelength;
   c->kb = c->k * sqrt(g->eps_b);
   const int d = g->dim;
-  c->tx_angles.assign(g->tx_angles, g->tx_angles + (d == 3 ? 3 * g->T : g->T));
+  c->tx_kind = g->tx_kind;
+  c->tx_angles.assign(g->tx_angles, g->tx_angles + (g->tx_kind == 1 ? (size_t)d * g->T : (d == 3 ? 3 * g->T : g->T)));
   c->rx_pos.assign(g->rx_pos, g->rx_pos + (size_t)d * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
@@ -616,6 +632,23 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
   st->k += 1;
   st->D = D;
   return s1;
+}
+
+cisor_status cisor_set_rx_mask(cisor_ctx* c, const void* mask) {
+  if (!c) {
+    set_error("cisor_set_rx_mask: NULL context");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (!mask) {
+    if (c->rx_mask) CISOR_CUDA(cudaFree(c->rx_mask));
+    c->rx_mask = nullptr;
+    return CISOR_OK;
+  }
+  if (!c->rx_mask) CISOR_CUDA(cudaMalloc((void**)&c->rx_mask, (size_t)c->T * c->M));
+  Call call(c);
+  CISOR_TRY(call.enter());
+  CISOR_TRY(call.in(c->rx_mask, mask, (size_t)c->T * c->M));
+  return call.leave();
 }
 
 cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {

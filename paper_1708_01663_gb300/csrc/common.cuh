@@ -76,7 +76,9 @@ struct cisor_ctx {
   long long rslab;        // R offset between z slabs (3D: P^2)
   long long rtstride;     // R elements per transmitter
   double delta, wavelength, eps_b, k, kb;
-  std::vector<double> tx_angles, rx_pos;  // 2D: [T] angles, [M, 2]; 3D: [T, 3] directions, [M, 3]
+  std::vector<double> tx_angles, rx_pos;  // 2D: [T] angles, [M, 2]; 3D: [T, 3] directions, [M, 3];
+                                          // point sources (tx_kind 1): [T, d] positions
+  int tx_kind;                            // 0 plane waves, 1 point / line sources
   int device;
   cudaStream_t stream;  // internal non-blocking stream; ordered against the caller's via events
   cudaStream_t user_stream;
@@ -94,6 +96,7 @@ struct cisor_ctx {
   float2 *z, *gz;     // H^H w and z + G^H v
   float2 *f, *fz, *grad, *work_n;  // [N]
   float2 *Y, *w, *yobs;          // [T, M]
+  unsigned char* rx_mask;        // [T, M] active receivers (NULL: all), set by cisor_set_rx_mask
   float2* sense_part;            // [ksplit, T, M]
   int ksplit;
   float* part;     // [T, nblk, DOT_SLOTS] float2

@@ -4,6 +4,7 @@
 //                  a complex GEMM [T x N] . [N x M] with split-K; the product
 //                  f .* u is formed while staging the tile.
 //  residual_and_D: w = Z - y, D = 1/2 sum |w|^2                  (Eq. 7, Prop. 1)
+//                  (w = 0 at receivers a transmitter does not record)
 //  sense_adjoint : z_t = H^H w_t and b_t = conj(f) .* z_t        (Eq. 13 right-hand side)
 //  grad_assemble : g = sum_t conj(u_t) .* (z_t + G^H v_t)        (Eq. 12 before Re)
 //                  and the gradient step s - gamma grad D        (Eq. 9 argument)
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(256) sense_fwd_kernel(const float2* __restrict
 
 __global__ void __launch_bounds__(256) sense_reduce_kernel(const float2* __restrict__ part, int ks, int T, int M,
                                                            const float2* __restrict__ y, float2* __restrict__ Z,
-                                                           float2* __restrict__ w, double* __restrict__ dsum) {
+                                                           float2* __restrict__ w, double* __restrict__ dsum,
+                                                           const unsigned char* __restrict__ mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   double d = 0.0;
   if (idx < T * M) {
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__(256) sense_reduce_kernel(const float2* __restr
     if (Z) Z[idx] = make_float2((float)sx, (float)sy);
     if (y) {
       const float2 yv = y[idx];
-      const double wx = sx - yv.x, wy = sy - yv.y;
+      const double on = (mask && !mask[idx]) ? 0.0 : 1.0;  // inactive receivers leave D and the adjoint
+      const double wx = on * (sx - yv.x), wy = on * (sy - yv.y);
       if (w) w[idx] = make_float2((float)wx, (float)wy);
       d = 0.5 * (wx * wx + wy * wy);
     }
@@ -199,7 +202,7 @@ cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float
   CISOR_CUDA(cudaGetLastError());
   const int tm = ntx * c->M;
   sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, nullptr, Z, nullptr,
-                                                               nullptr);
+                                                               nullptr, nullptr);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 2;
   return CISOR_OK;
@@ -214,7 +217,8 @@ cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, cons
   CISOR_CUDA(cudaGetLastError());
   CISOR_CUDA(cudaMemsetAsync(c->dsum, 0, sizeof(double), c->stream));
   const int tm = ntx * c->M;
-  sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, y, Z, w, c->dsum);
+  sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, y, Z, w, c->dsum,
+                                                               c->rx_mask);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 2;
   return CISOR_OK;

@@ -195,6 +195,31 @@ __global__ void plane_wave3d_kernel(float2* u, const double* dir, int T, int n, 
   u[idx] = make_float2((float)c, (float)s);
 }
 
+// Field of a unit point (3D) or line (2D) source at src_t: g(|r - src_t|) of
+// Eq. 1 without the quadrature weight k^2 delta^d.  Sources lie outside the grid.
+__global__ void point_source_kernel(float2* u, const double* src, int T, int n, int dim, double delta, double kb) {
+  const long long N = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)T * N) return;
+  const int t = (int)(idx / N);
+  const long long p = idx % N;
+  const double h = n / 2.0 - 0.5;
+  const double x = ((int)(p % n) - h) * delta, y = ((int)((p / n) % n) - h) * delta;
+  const double z = dim == 3 ? ((int)(p / ((long long)n * n)) - h) * delta : 0.0;
+  const double dx = src[dim * t] - x, dy = src[dim * t + 1] - y, dz = dim == 3 ? src[3 * t + 2] - z : 0.0;
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double2 g;
+  if (dim == 3) {
+    double sn, cs;
+    sincos(kb * r, &sn, &cs);
+    const double s = 1.0 / (4.0 * 3.14159265358979323846 * r);
+    g = make_double2(s * cs, s * sn);
+  } else {
+    g = make_double2(-0.25 * y0(kb * r), 0.25 * j0(kb * r));  // (j/4)(J0 + j Y0)
+  }
+  u[idx] = make_float2((float)g.x, (float)g.y);
+}
+
 __global__ void plane_wave_kernel(float2* u, const double* ang, int T, int n, double delta, double kb) {
   long long N = (long long)n * n;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,16 +332,18 @@ cisor_status build_tables(cisor_ctx* c) {
   }
   long long MN = (long long)c->M * c->N;
   long long TN = (long long)c->T * c->N;
-  if (d == 3) {
+  if (d == 3)
     sensing3d_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
-    CISOR_CUDA(cudaGetLastError());
-    plane_wave3d_kernel<<<(unsigned)((TN + 255) / 256), 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta,
-                                                                             c->kb);
-  } else {
+  else
     sensing_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
-    CISOR_CUDA(cudaGetLastError());
-    plane_wave_kernel<<<(unsigned)((TN + 255) / 256), 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta, c->kb);
-  }
+  CISOR_CUDA(cudaGetLastError());
+  const unsigned gT = (unsigned)((TN + 255) / 256);
+  if (c->tx_kind == 1)
+    point_source_kernel<<<gT, 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, d, c->delta, c->kb);
+  else if (d == 3)
+    plane_wave3d_kernel<<<gT, 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta, c->kb);
+  else
+    plane_wave_kernel<<<gT, 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta, c->kb);
   CISOR_CUDA(cudaGetLastError());
   CISOR_CUDA(cudaFreeAsync(cbuf, c->stream));
   CISOR_CUDA(cudaFreeAsync(tw64, c->stream));

@@ -154,6 +154,21 @@ def planar_receivers(side: int, pitch: float, z: float) -> np.ndarray:
     return np.stack([X.ravel(), Y.ravel(), np.full(side * side, z)], axis=1)
 
 
+def circle_sources(T: int, radius: float, offset: float = 0.0) -> np.ndarray:
+    """[T, 2] source positions uniformly spaced on a circle, starting at angle ``offset``."""
+    phi = offset + 2.0 * np.pi * np.arange(T) / T
+    return np.stack([radius * np.cos(phi), radius * np.sin(phi)], axis=1)
+
+
+def angular_mask(src: np.ndarray, rx: np.ndarray, min_deg: float) -> np.ndarray:
+    """[T, M] 0/1 mask: receiver m is active for source t when their directions
+    from the origin differ by more than ``min_deg`` degrees."""
+    a = np.arctan2(src[:, 1], src[:, 0])[:, None]
+    b = np.arctan2(rx[:, 1], rx[:, 0])[None, :]
+    d = np.abs((b - a + np.pi) % (2.0 * np.pi) - np.pi)
+    return (d > np.radians(min_deg)).astype(np.uint8)
+
+
 def complex_noise(seed: int, shape) -> np.ndarray:
     """Unit-variance circular complex Gaussian draws (a + ib)/sqrt(2)."""
     cnt = int(np.prod(shape))
@@ -189,6 +204,15 @@ CONFIGS = {
     "c3": dict(dim=3, n=64, delta=1.0 / 6, T=48, M=1024, rx_plane=8.0, shapes=5,
                contrast=(0.0, 0.3), imag=0.0, snr_db=40.0, outer=50, tau=1e-3,
                tv_iters=20, alpha=0.96, seed=1711),
+    # 2D Fresnel-style: the sizes of the 2D experimental set-up of Sec. IV at
+    # 3 GHz (lambda = 100 mm): a 150 mm domain on 128 x 128 pixels (delta =
+    # 1.5 lambda / 128), 8 line sources on a circle of 7.2 lambda, 360
+    # receivers on a circle of 7.6 lambda, each source recording the receivers
+    # more than 60 degrees away from it (240 of 360); 3 seeded ellipses with
+    # real contrast up to 1.0 stand in for the measured objects.
+    "c6": dict(dim=2, n=128, delta=1.5 / 128, T=8, M=360, rx_radius=7.6, tx_radius=7.2, tx_kind="point",
+               rx_min_deg=60.0, shapes=3, contrast=(0.0, 1.0), imag=0.0, snr_db=40.0, outer=100, tau=1e-3,
+               tv_iters=20, alpha=0.96, seed=1714),
 }
 
 
@@ -202,6 +226,12 @@ def make_inputs(name: str, T: int | None = None):
         tx = hemisphere_directions()[: cfg["T"]]
         rx = planar_receivers(32, 0.5, cfg["rx_plane"])
         return cfg, f, tx, rx
+    if cfg.get("tx_kind") == "point":
+        f = ellipse_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
+        src = circle_sources(CONFIGS[name]["T"], cfg["tx_radius"])[: cfg["T"]]
+        rx = circle_receivers(cfg["M"], cfg["rx_radius"])
+        cfg["rx_mask"] = angular_mask(src, rx, cfg["rx_min_deg"])
+        return cfg, f, src, rx
     f = ellipse_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
     angles = plane_wave_angles(CONFIGS[name]["T"])[: cfg["T"]]
     rx = circle_receivers(cfg["M"], cfg["rx_radius"])
