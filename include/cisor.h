@@ -99,6 +99,8 @@ typedef struct {
   double lo, hi;    /* box C for Re f */
   double lo_im, hi_im; /* box C for Im f (complex_f only) */
   double D;         /* out: D(s_k) of Eq. 7 */
+  int tv_kind;      /* 0: isotropic TV of Eq. 8 by FGP; 1: anisotropic TV by the parallel proximal
+                       algorithm (cisor_tv_prox_aniso) */
 } cisor_fista_state;
 
 /* Build the tables of a geometry on the current CUDA device: the spectrum of
@@ -169,6 +171,13 @@ cisor_status cisor_data_backward(cisor_ctx* ctx, void* grad_out, const cisor_sol
  * Im (separable prox); for real f Im x = 0.  z, x: [N] complex64. */
 cisor_status cisor_tv_prox(cisor_ctx* ctx, const void* z, void* x, double gamma_tau, int iters, double lo,
                            double hi, double lo_im, double hi_im);
+
+/* As cisor_tv_prox for the anisotropic TV, sum_d sum_n |[D_d x]_n| (the
+ * alternative Sec. III-A points to), by `iters` iterations of the parallel
+ * Dykstra-like proximal algorithm over the 2 dim pair-difference pieces and
+ * the box; dual-free, cold start. */
+cisor_status cisor_tv_prox_aniso(cisor_ctx* ctx, const void* z, void* x, double gamma_tau, int iters, double lo,
+                                 double hi, double lo_im, double hi_im);
 
 /* One relaxed-FISTA iteration (Eqs. 9-11) on the state; y: [T, M] measurements.
  * Inner solves use opts (x0_mode 2 warm-starts from the previous step). */

@@ -45,7 +45,7 @@ class SolveInfo(Structure):
 class FistaState(Structure):
     _fields_ = [("f", c_void_p), ("s", c_void_p), ("t", c_double), ("k", c_int), ("alpha", c_double),
                 ("gamma", c_double), ("tau", c_double), ("tv_iters", c_int), ("lo", c_double),
-                ("hi", c_double), ("lo_im", c_double), ("hi_im", c_double), ("D", c_double)]
+                ("hi", c_double), ("lo_im", c_double), ("hi_im", c_double), ("D", c_double), ("tv_kind", c_int)]
 
 
 class CisorError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "cisor_sense_adjoint": [vp, vp, vp, vp, vp],
         "cisor_grad": [vp, vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_tv_prox": [vp, vp, vp, d, i, d, d, d, d],
+        "cisor_tv_prox_aniso": [vp, vp, vp, d, i, d, d, d, d],
         "cisor_step": [vp, POINTER(FistaState), vp, POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_step_update": [vp, POINTER(FistaState), vp, c_double],
         "cisor_set_cols_cta": [vp, c_int],
@@ -314,14 +315,16 @@ class Cisor:
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return st, info
 
-    def tv_prox(self, z, x, gamma_tau, iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5):
-        return _check(self._lib.cisor_tv_prox(self._ctx, ptr(z, self.N), ptr(x, self.N), float(gamma_tau),
-                                              int(iters), float(lo), float(hi), float(lo_im), float(hi_im)))
+    def tv_prox(self, z, x, gamma_tau, iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5, aniso=False):
+        fn = self._lib.cisor_tv_prox_aniso if aniso else self._lib.cisor_tv_prox
+        return _check(fn(self._ctx, ptr(z, self.N), ptr(x, self.N), float(gamma_tau), int(iters), float(lo),
+                         float(hi), float(lo_im), float(hi_im)))
 
-    def new_state(self, f, s, alpha, gamma, tau, tv_iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5):
-        """Relaxed-FISTA state over caller-owned f and s arrays (t = 1, k = 1)."""
+    def new_state(self, f, s, alpha, gamma, tau, tv_iters, lo=0.0, hi=2.0, lo_im=0.0, hi_im=0.5, tv_kind=0):
+        """Relaxed-FISTA state over caller-owned f and s arrays (t = 1, k = 1);
+        tv_kind 1 selects the anisotropic TV prox."""
         st = FistaState(ptr(f, self.N), ptr(s, self.N), 1.0, 1, alpha, gamma, tau, tv_iters, lo, hi, lo_im, hi_im,
-                        0.0)
+                        0.0, int(tv_kind))
         st._keep = (f, s)
         return st
 

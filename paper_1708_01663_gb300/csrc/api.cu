@@ -165,7 +165,7 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -315,6 +315,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->tv_r0, sizeof(float) * 2 * d * c->N);
   ALLOC(c->tv_r1, sizeof(float) * 2 * d * c->N);
   ALLOC(c->tv_p, sizeof(float) * 2 * d * c->N);
+  ALLOC(c->tva0, sizeof(float) * 2 * (2 * d + 1) * c->N);
+  ALLOC(c->tva1, sizeof(float) * 2 * (2 * d + 1) * c->N);
 #undef ALLOC
   {
     cudaError_t e = cudaMallocHost((void**)&c->h_active, sizeof(int) * c->T);
@@ -548,8 +550,8 @@ cisor_status cisor_data_backward(cisor_ctx* c, void* grad_out, const cisor_solve
   return st;
 }
 
-cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo, double hi,
-                           double lo_im, double hi_im) {
+static cisor_status tv_prox_entry(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo,
+                                  double hi, double lo_im, double hi_im, int aniso) {
   if (!c || !z || !x || iters < 0 || !(lo <= hi) || (c && c->complex_f && !(lo_im <= hi_im))) {
     set_error("cisor_tv_prox: NULL argument, negative iteration count or empty box");
     return CISOR_ERR_INVALID_ARG;
@@ -557,14 +559,26 @@ cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_ta
   Call call(c);
   CISOR_TRY(call.enter());
   CISOR_TRY(call.in(c->fz, z, sizeof(float2) * c->N));
-  CISOR_TRY(tv_prox(c, c->fz, c->work_n, gamma_tau, iters, lo, hi, lo_im, hi_im, c->complex_f, nullptr, 0.0, nullptr));
+  auto prox = aniso ? tv_prox_aniso : tv_prox;
+  CISOR_TRY(prox(c, c->fz, c->work_n, gamma_tau, iters, lo, hi, lo_im, hi_im, c->complex_f, nullptr, 0.0, nullptr));
   CISOR_TRY(call.out(x, c->work_n, sizeof(float2) * c->N));
   return call.leave();
 }
 
+cisor_status cisor_tv_prox(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo, double hi,
+                           double lo_im, double hi_im) {
+  return tv_prox_entry(c, z, x, gamma_tau, iters, lo, hi, lo_im, hi_im, 0);
+}
+
+cisor_status cisor_tv_prox_aniso(cisor_ctx* c, const void* z, void* x, double gamma_tau, int iters, double lo,
+                                 double hi, double lo_im, double hi_im) {
+  return tv_prox_entry(c, z, x, gamma_tau, iters, lo, hi, lo_im, hi_im, 1);
+}
+
 static bool state_ok(const cisor_ctx* c, const cisor_fista_state* st, const char* who) {
   if (!(st->alpha >= 0.0 && st->alpha <= 1.0) || !(st->gamma > 0.0) || !(st->tau >= 0.0) || st->tv_iters < 0 ||
-      !(st->lo <= st->hi) || (c->complex_f && !(st->lo_im <= st->hi_im)) || !(st->t >= 1.0)) {
+      !(st->lo <= st->hi) || (c->complex_f && !(st->lo_im <= st->hi_im)) || !(st->t >= 1.0) ||
+      (st->tv_kind != 0 && st->tv_kind != 1)) {
     set_error("%s: invalid state (alpha %g, gamma %g, tau %g, t %g)", who, st->alpha, st->gamma, st->tau, st->t);
     return false;
   }
@@ -576,8 +590,9 @@ static cisor_status prox_and_momentum(cisor_ctx* c, cisor_fista_state* st, doubl
   const double t = st->t;
   const double tn = (sqrt(4.0 * t * t + 1.0) + 1.0) / 2.0;
   const double beta = st->alpha * (t - 1.0) / tn;
-  CISOR_TRY(tv_prox(c, c->fz, c->work_n, st->gamma * st->tau, st->tv_iters, st->lo, st->hi, st->lo_im, st->hi_im,
-                    c->complex_f, c->work_n, beta, c->f));
+  auto prox = st->tv_kind == 1 ? tv_prox_aniso : tv_prox;
+  CISOR_TRY(prox(c, c->fz, c->work_n, st->gamma * st->tau, st->tv_iters, st->lo, st->hi, st->lo_im, st->hi_im,
+                 c->complex_f, c->work_n, beta, c->f));
   *tn_out = tn;
   return CISOR_OK;
 }

@@ -108,6 +108,7 @@ struct cisor_ctx {
   double* h_dsum;   // pinned [4]
   // TV workspace (d dual components x N floats per plane, up to 2 planes)
   float *tv_z, *tv_r0, *tv_r1, *tv_p;
+  float *tva0, *tva1;  // anisotropic TV: (2d + 1) auxiliary images per plane, ping-pong
   // graphs of a chunk of BiCGSTAB iterations
   cudaGraphExec_t graph[2];
   int graph_ntx[2];
@@ -209,5 +210,8 @@ cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, doubl
 cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,
                      double lo_im, double hi_im, int complex_f, const float2* f_prev, double beta_mom,
                      float2* s_out);
+cisor_status tv_prox_aniso(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,
+                           double lo_im, double hi_im, int complex_f, const float2* f_prev, double beta_mom,
+                           float2* s_out);
 
 }  // namespace cisor

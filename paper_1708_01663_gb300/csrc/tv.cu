@@ -15,6 +15,17 @@
 // s_{k+1} = f_k + beta (f_k - f_{k-1}).
 // 3D volumes take the same iteration with p = (p_x, p_y, p_z), the unit-ball
 // projection in R^3 and the dual step 1 / (12 lam) (||D||^2 <= 4 d).
+//
+// Anisotropic TV (tv_kind 1): R = tau sum_d sum_n |[D_d x]_n| + chi_C, the
+// alternative Sec. III-A points to (Kamilov, IEEE TIP 2017).  Along each axis
+// the differences split into pairs (i, i+1) with i even and with i odd; each
+// parity is a sum over disjoint pairs whose prox keeps the pair's mean and
+// soft-thresholds its difference by 2c.  With the box, m = 2d + 1 pieces f_j,
+// and prox_{sum f_j}(z) comes from the parallel Dykstra-like proximal
+// iteration (Combettes and Pesquet 2011): z_j = z; repeat p_j = prox_{m f_j}(z_j),
+// x = mean_j p_j, z_j += x - p_j.  Every step is pointwise (a pixel needs its
+// pair partner along each axis), so one kernel per iteration, ping-ponging the
+// 2d + 1 auxiliary images between two buffers.
 #include <math.h>
 
 #include "common.cuh"
@@ -157,6 +168,107 @@ __global__ void tv_final_kernel(const float* __restrict__ zp, const float* __res
     s_out[i] = make_float2(xo.x + beta_mom * (xo.x - fp.x), xo.y + beta_mom * (xo.y - fp.y));
   }
   x[i] = xo;
+}
+
+// z_j = z for every piece j of every plane: layout (plane * m + j) * N
+__global__ void tv_ppa_init_kernel(const float2* __restrict__ z, float* __restrict__ zs, long long N, int m,
+                                   int ncomp) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float2 v = z[i];
+  for (int c = 0; c < ncomp; ++c)
+    for (int j = 0; j < m; ++j) zs[((long long)c * m + j) * N + i] = c ? v.y : v.x;
+}
+
+__device__ __forceinline__ float soft(float d, float t) { return copysignf(fmaxf(fabsf(d) - t, 0.f), d); }
+
+template <int D>
+__global__ void __launch_bounds__(256) tv_ppa_kernel(const float* __restrict__ zin, float* __restrict__ zout, int n,
+                                                     float cthr, float lo0, float hi0, float lo1, float hi1, int ncomp,
+                                                     int last, float2* x_out, const float2* fprev, float beta_mom,
+                                                     float2* __restrict__ s_out) {
+  constexpr int M = 2 * D + 1;
+  const long long nn = (long long)n * n;
+  const long long N = D == 3 ? nn * n : nn;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int coord[3] = {(int)(i % n), (int)((i / n) % n), (int)(i / nn)};
+  const long long stride[3] = {1, n, nn};
+  float xv[2] = {0.f, 0.f};
+  for (int c = 0; c < ncomp; ++c) {
+    const float* zc = zin + (long long)c * M * N;
+    float zj[M], p[M];
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2 * D; ++j) {
+      const int a = j >> 1, par = j & 1, pos = coord[a];
+      const float* zp = zc + (long long)j * N;
+      const float v = zp[i];
+      zj[j] = v;
+      const int rel = pos - par;
+      float pj = v;
+      if (rel >= 0 && (rel & 1) == 0 && pos + 1 < n) {  // first of the pair (pos, pos + 1)
+        const float w = zp[i + stride[a]];
+        pj = 0.5f * (v + w) - 0.5f * soft(w - v, 2.f * cthr);
+      } else if (rel >= 1 && (rel & 1) == 1) {          // second of the pair (pos - 1, pos)
+        const float w = zp[i - stride[a]];
+        pj = 0.5f * (w + v) + 0.5f * soft(v - w, 2.f * cthr);
+      }
+      p[j] = pj;
+      acc += pj;
+    }
+    const float lo = c ? lo1 : lo0, hi = c ? hi1 : hi0;
+    zj[2 * D] = zc[(long long)(2 * D) * N + i];
+    p[2 * D] = fminf(fmaxf(zj[2 * D], lo), hi);
+    acc += p[2 * D];
+    const float x = acc * (1.f / M);
+    xv[c] = x;
+    if (!last) {
+      float* zo = zout + (long long)c * M * N;
+#pragma unroll
+      for (int j = 0; j < M; ++j) zo[(long long)j * N + i] = x + zj[j] - p[j];
+    }
+  }
+  if (last) {
+    const float2 xo = make_float2(xv[0], xv[1]);
+    if (s_out) {
+      const float2 fp = fprev[i];  // read before x (x may alias fprev)
+      s_out[i] = make_float2(xo.x + beta_mom * (xo.x - fp.x), xo.y + beta_mom * (xo.y - fp.y));
+    }
+    x_out[i] = xo;
+  }
+}
+
+cisor_status tv_prox_aniso(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,
+                           double lo_im, double hi_im, int complex_f, const float2* f_prev, double beta_mom,
+                           float2* s_out) {
+  if (!(lam > 0.0) || iters < 1)  // the prox of the box alone is the clamp (the FGP path's last kernel)
+    return tv_prox(c, z, x, 0.0, 0, lo, hi, lo_im, hi_im, complex_f, f_prev, beta_mom, s_out);
+  const long long N = c->N;
+  const int ncomp = complex_f ? 2 : 1;
+  const int m = 2 * c->dim + 1;
+  const unsigned gN = (unsigned)((N + 255) / 256);
+  tv_ppa_init_kernel<<<gN, 256, 0, c->stream>>>(z, c->tva0, N, m, ncomp);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  float* zin = c->tva0;
+  float* zout = c->tva1;
+  const float cthr = (float)(m * lam);
+  for (int k = 0; k < iters; ++k) {
+    const int last = k == iters - 1;
+    if (c->dim == 3)
+      tv_ppa_kernel<3><<<gN, 256, 0, c->stream>>>(zin, zout, c->n, cthr, (float)lo, (float)hi, (float)lo_im,
+                                                  (float)hi_im, ncomp, last, x, f_prev, (float)beta_mom, s_out);
+    else
+      tv_ppa_kernel<2><<<gN, 256, 0, c->stream>>>(zin, zout, c->n, cthr, (float)lo, (float)hi, (float)lo_im,
+                                                  (float)hi_im, ncomp, last, x, f_prev, (float)beta_mom, s_out);
+    CISOR_CUDA(cudaGetLastError());
+    c->launches += 1;
+    float* t = zin;
+    zin = zout;
+    zout = t;
+  }
+  return CISOR_OK;
 }
 
 cisor_status tv_prox(cisor_ctx* c, const float2* z, float2* x, double lam, int iters, double lo, double hi,

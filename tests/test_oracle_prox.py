@@ -1,4 +1,6 @@
 """Pins of the oracle's constrained isotropic-TV prox (Eq. 8 through FGP)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -76,3 +78,83 @@ def test_objective_decreases_with_iterations():
     vals = [_objective(prox.fgp(z, lam, k, 0.0, 2.0), z, lam) for k in (5, 20, 100, 1000)]
     assert vals[-1] <= min(vals) + 1e-12
     assert vals[1] - vals[-1] < 0.1 * (vals[0] - vals[-1] + 1e-12) + 1e-3
+
+
+# ---------------------------------------------------------------- anisotropic TV (parallel proximal)
+def _aniso_dual_reference(z, lam, iters=20000):
+    """Exact prox of lam * TV_aniso (no box) by accelerated projected gradient on
+    the dual: x = z - D^T p, p_d in [-lam, lam] per pixel (a different algorithm)."""
+    nd = z.ndim
+    def D(x):
+        out = []
+        for a in range(nd):
+            d = np.zeros_like(x)
+            sl_hi = [slice(None)] * nd; sl_hi[a] = slice(1, None)
+            sl_lo = [slice(None)] * nd; sl_lo[a] = slice(None, -1)
+            d[tuple(sl_lo)] = x[tuple(sl_hi)] - x[tuple(sl_lo)]
+            out.append(d)
+        return out
+    def DT(ps):
+        out = np.zeros_like(ps[0])
+        for a, p in enumerate(ps):
+            sl_hi = [slice(None)] * nd; sl_hi[a] = slice(1, None)
+            sl_lo = [slice(None)] * nd; sl_lo[a] = slice(None, -1)
+            out[tuple(sl_lo)] -= p[tuple(sl_lo)]
+            out[tuple(sl_hi)] += p[tuple(sl_lo)]
+        return out
+    p = [np.zeros_like(z) for _ in range(nd)]
+    q = [pi.copy() for pi in p]
+    t = 1.0
+    step = 1.0 / (4.0 * nd)
+    for _ in range(iters):
+        g = D(z - DT(q))
+        pn = [np.clip(qi + step * gi, -lam, lam) for qi, gi in zip(q, g)]
+        tn = (1 + math.sqrt(1 + 4 * t * t)) / 2
+        q = [a + ((t - 1) / tn) * (a - b) for a, b in zip(pn, p)]
+        p, t = pn, tn
+    return z - DT(p)
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (6, 5, 7)])
+def test_ppa_aniso_converges_to_exact_prox(shape):
+    z = synth.random_field(31, shape).real
+    lam = 0.3
+    ref = _aniso_dual_reference(z, lam)
+    x = prox.ppa_aniso(z, lam, 3000)
+    assert np.abs(x - ref).max() < 1e-5
+    # optimality margin: the reference is the minimiser of the prox objective
+    obj = lambda v: 0.5 * np.sum((v - z) ** 2) + lam * prox.tv_aniso(v)
+    assert abs(obj(x) - obj(ref)) < 1e-8 * obj(ref) + 1e-10
+
+
+def test_ppa_aniso_wrong_threshold_fails():
+    # a planted mistake (threshold lam instead of m lam in the pieces) does not reach the prox
+    z = synth.random_field(32, (10, 9)).real
+    ref = _aniso_dual_reference(z, 0.3)
+    pieces = [(a, par) for a in range(2) for par in (0, 1)]
+    zs = [z.copy() for _ in range(5)]
+    for _ in range(2000):
+        ps = [prox.pair_shrink(zs[j], a, par, 0.3) for j, (a, par) in enumerate(pieces)] + [zs[-1]]
+        x = sum(ps) / 5
+        zs = [x + zj - pj for zj, pj in zip(zs, ps)]
+    assert np.abs(x - ref).max() > 1e-2
+
+
+def test_ppa_aniso_plateau_closed_form_and_limits():
+    W, a, b, lam = 16, 0.2, 1.0, 0.4
+    z = np.full((5, W), a)
+    z[:, W // 2:] = b
+    x = prox.ppa_aniso(z, lam, 4000, -10, 10)
+    assert np.abs(x[:, : W // 2] - (a + 2 * lam / W)).max() < 1e-6
+    assert np.abs(x[:, W // 2:] - (b - 2 * lam / W)).max() < 1e-6
+    zz = synth.random_field(5, (8, 8)).real
+    assert np.array_equal(prox.ppa_aniso(zz, 0.0, 10, -0.5, 0.5), np.clip(zz, -0.5, 0.5))
+    c = np.full((6, 7), 0.7)
+    assert np.allclose(prox.ppa_aniso(c, 0.5, 50, 0.0, 2.0), c, atol=1e-12)
+
+
+def test_ppa_aniso_respects_box():
+    z = 2.0 * synth.random_field(33, (9, 9)).real
+    x = prox.ppa_aniso(z, 0.1, 3000, -0.5, 0.8)
+    # Dykstra-type iterations reach the box only in the limit
+    assert x.min() > -0.5 - 1e-4 and x.max() < 0.8 + 1e-4
