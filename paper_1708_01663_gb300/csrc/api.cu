@@ -253,8 +253,9 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->cols_nt = 512;
   conv_geometry(c);
   {
-    const int tiles = ((c->M + 63) / 64) * ((c->T + 31) / 32);
-    int ks = (2 * 152 + tiles - 1) / tiles;
+    // split-K of the forward sensing GEMM: about 4 CTAs per SM, chunks of >= 256 pixels
+    const int tiles = sense_tiles(c->M, c->T);
+    int ks = (4 * 152 + tiles - 1) / tiles;
     const int kmax = (int)((c->N + 255) / 256);
     c->ksplit = ks < 1 ? 1 : (ks > kmax ? kmax : ks);
   }

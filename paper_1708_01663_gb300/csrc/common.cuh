@@ -32,6 +32,22 @@ __host__ __device__ __forceinline__ float2 c_scale(float2 a, float s) { return m
 __host__ __device__ __forceinline__ float2 c_cjmul(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// acc + a * b and acc + conj(a) * b as four FMAs (a product formed first and
+// then added would take an extra rounding and two more instructions)
+__host__ __device__ __forceinline__ float2 c_fma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__host__ __device__ __forceinline__ float2 c_cjfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
 __host__ __device__ __forceinline__ double2 z_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ double2 z_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __host__ __device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
@@ -198,6 +214,7 @@ cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2
                          MultiSolve& ms, SolveStat* st);
 
 // sense.cu
+int sense_tiles(int M, int T);  // CTA tiles of the forward sensing GEMM (before split-K)
 cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Y, int ntx);
 cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, const float2* y, float2* Z, float2* w,
                             int ntx);

@@ -15,59 +15,90 @@
 
 namespace cisor {
 
-constexpr int GT = 32;  // transmitters per CTA tile
-constexpr int GM = 64;  // receivers (forward) / pixels (adjoint) per CTA tile
-constexpr int GK = 32;  // reduction tile
+// Tiles of the two complex GEMMs: 32 transmitters x 128 receivers (forward) or
+// pixels (adjoint) per CTA, 16 along the reduction.  Thread (tx, ty) = (lane,
+// warp) owns transmitters ty + 8i and receivers / pixels tx + 32j (i, j < 4):
+// the transmitter operand is a warp-wide broadcast and the other one is read
+// at consecutive addresses, so the shared-memory reads are conflict-free; the
+// transposed stores use a pitch of 129 / 33 elements.  Tiles are staged
+// through registers one step ahead (double buffer, one barrier per step).
+constexpr int GT = 32;   // transmitters per CTA tile
+constexpr int GM = 128;  // receivers (forward) / pixels (adjoint) per CTA tile
+constexpr int GK = 16;   // reduction tile
 
-__global__ void __launch_bounds__(256) sense_fwd_kernel(const float2* __restrict__ H, const float2* __restrict__ f,
+int sense_tiles(int M, int T) { return ((M + GM - 1) / GM) * ((T + GT - 1) / GT); }
+
+__global__ void __launch_bounds__(256, 2) sense_fwd_kernel(const float2* __restrict__ H, const float2* __restrict__ f,
                                                         const float2* __restrict__ u, float2* __restrict__ part, int T,
                                                         int M, long long N, long long chunk) {
-  __shared__ float2 Qs[GK][GT + 1];
-  __shared__ float2 Hs[GK][GM + 1];
+  __shared__ float2 Hs[2][GK][GM + 1];
+  __shared__ float2 Qs[2][GK][GT + 1];
   const int m0 = blockIdx.x * GM, t0 = blockIdx.y * GT, ks = blockIdx.z;
   const long long kb = (long long)ks * chunk;
   const long long ke = min(N, kb + chunk);
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  float2 acc[4][2];
+  float2 hr[8], qr[2];
+  auto load = [&](long long k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q, kk = e & (GK - 1), mm = e >> 4;
+      const long long k = k0 + kk;
+      const int m = m0 + mm;
+      hr[q] = (k < ke && m < M) ? H[(long long)m * N + k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + 256 * q, kk = e & (GK - 1), tt = e >> 4;
+      const long long k = k0 + kk;
+      const int t = t0 + tt;
+      qr[q] = (k < ke && t < T) ? c_mul(f[k], u[(long long)t * N + k]) : make_float2(0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 256 * q;
+      Hs[buf][e & (GK - 1)][e >> 4] = hr[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + 256 * q;
+      Qs[buf][e & (GK - 1)][e >> 4] = qr[q];
+    }
+  };
+  float2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  load(kb);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
   for (long long k0 = kb; k0 < ke; k0 += GK) {
+    const bool more = k0 + GK < ke;
+    if (more) load(k0 + GK);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + 256 * q, kk = e & 31, mm = e >> 5;
-      const long long k = k0 + kk;
-      const int m = m0 + mm;
-      Hs[kk][mm] = (k < ke && m < M) ? H[(long long)m * N + k] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q, kk = e & 31, tt = e >> 5;
-      const long long k = k0 + kk;
-      const int t = t0 + tt;
-      Qs[kk][tt] = (k < ke && t < T) ? c_mul(f[k], u[(long long)t * N + k]) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll 8
     for (int kk = 0; kk < GK; ++kk) {
-      float2 a[4], b[2];
+      float2 a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = Qs[kk][ty * 4 + i];
+      for (int i = 0; i < 4; ++i) a[i] = Qs[buf][kk][ty + 8 * i];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) b[j] = Hs[kk][tx * 2 + j];
+      for (int j = 0; j < 4; ++j) b[j] = Hs[buf][kk][tx + 32 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) acc[i][j] = c_add(acc[i][j], c_mul(a[i], b[j]));
+        for (int j = 0; j < 4; ++j) acc[i][j] = c_fma(a[i], b[j], acc[i][j]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int t = t0 + ty * 4 + i, m = m0 + tx * 2 + j;
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + ty + 8 * i, m = m0 + tx + 32 * j;
       if (t < T && m < M) part[((long long)ks * T + t) * M + m] = acc[i][j];
     }
 }
@@ -107,54 +138,77 @@ __global__ void __launch_bounds__(256) sense_reduce_kernel(const float2* __restr
   }
 }
 
-__global__ void __launch_bounds__(256) sense_adj_kernel(const float2* __restrict__ H, const float2* __restrict__ w,
+// One stage of the adjoint's operand tiles: H rows m0..m0+15 at pixels n0..n0+127
+// (coalesced along n) and w of the 32 transmitters at those receivers.
+__device__ __forceinline__ void adj_load(const float2* __restrict__ H, const float2* __restrict__ w, int tid, int m0,
+                                         long long n0, int t0, int T, int M, long long N, float2 (&hr)[8],
+                                         float2 (&wr)[2]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + 256 * q, nn = e & (GM - 1), mm = e >> 7;
+    const int m = m0 + mm;
+    const long long n = n0 + nn;
+    hr[q] = (m < M && n < N) ? H[(long long)m * N + n] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = tid + 256 * q, mm = e & (GK - 1), tt = e >> 4;
+    const int m = m0 + mm, t = t0 + tt;
+    wr[q] = (m < M && t < T) ? w[(long long)t * M + m] : make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) sense_adj_kernel(const float2* __restrict__ H, const float2* __restrict__ w,
                                                         const float2* __restrict__ f, float2* __restrict__ z,
                                                         float2* __restrict__ b, int T, int M, long long N) {
-  __shared__ float2 Hs[GK][GM];
-  __shared__ float2 Ws[GK][GT + 1];
+  __shared__ float2 Hs[2][GK][GM];
+  __shared__ float2 Ws[2][GK][GT + 1];
   const long long n0 = (long long)blockIdx.x * GM;
   const int t0 = blockIdx.y * GT;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  float2 acc[4][2];
+  float2 hr[8], wr[2];
+  float2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  adj_load(H, w, tid, 0, n0, t0, T, M, N, hr, wr);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) Hs[0][(tid + 256 * q) >> 7][(tid + 256 * q) & (GM - 1)] = hr[q];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) Ws[0][(tid + 256 * q) & (GK - 1)][(tid + 256 * q) >> 4] = wr[q];
+  __syncthreads();
+  int buf = 0;
   for (int m0 = 0; m0 < M; m0 += GK) {
+    const bool more = m0 + GK < M;
+    if (more) adj_load(H, w, tid, m0 + GK, n0, t0, T, M, N, hr, wr);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + 256 * q, nn = e & 63, mm = e >> 6;
-      const int m = m0 + mm;
-      const long long n = n0 + nn;
-      Hs[mm][nn] = (m < M && n < N) ? H[(long long)m * N + n] : make_float2(0.f, 0.f);
-    }
+    for (int kk = 0; kk < GK; ++kk) {
+      float2 a[4], h[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q, mm = e & 31, tt = e >> 5;
-      const int m = m0 + mm, t = t0 + tt;
-      Ws[mm][tt] = (m < M && t < T) ? w[(long long)t * M + m] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int mm = 0; mm < GK; ++mm) {
-      float2 a[4], h[2];
+      for (int i = 0; i < 4; ++i) a[i] = Ws[buf][kk][ty + 8 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = Ws[mm][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) h[j] = Hs[mm][tx * 2 + j];
+      for (int j = 0; j < 4; ++j) h[j] = Hs[buf][kk][tx + 32 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) acc[i][j] = c_add(acc[i][j], c_cjmul(h[j], a[i]));
+        for (int j = 0; j < 4; ++j) acc[i][j] = c_cjfma(h[j], a[i], acc[i][j]);
+    }
+    if (more) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Hs[buf ^ 1][(tid + 256 * q) >> 7][(tid + 256 * q) & (GM - 1)] = hr[q];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) Ws[buf ^ 1][(tid + 256 * q) & (GK - 1)][(tid + 256 * q) >> 4] = wr[q];
     }
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int t = t0 + ty * 4 + i;
-      const long long n = n0 + tx * 2 + j;
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + ty + 8 * i;
+      const long long n = n0 + tx + 32 * j;
       if (t < T && n < N) {
         const long long idx = (long long)t * N + n;
         if (z) z[idx] = acc[i][j];
