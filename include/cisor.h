@@ -63,6 +63,10 @@ typedef struct {
   int complex_f;            /* 0: f real (Im f is neither updated nor regularised); 1: complex f */
   int pad;                  /* FFT side P >= 2n - 1, a power of two <= 512 (2D) / 256 (3D); 0 = smallest such */
   int tx_kind;              /* 0: plane waves; 1: point / line sources */
+  int vectorial;            /* 1: the 3D vectorial model of the appendix (dim 3, eps_b = 1, n <= 64):
+                               fields are [T, 3, N] (E^(1), E^(2), E^(3)), tx_angles is [T, 6]
+                               (unit direction, unit polarisation orthogonal to it), H is [M, 3N]
+                               (z component at the receivers); 0: the scalar model */
 } cisor_geometry;
 
 /* Options of the field solves A u = u_in and A^H v = b (Eq. 13). */

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "BREAKDOWN", 4
 class Geometry(Structure):
     _fields_ = [("dim", c_int), ("n", c_int), ("delta", c_double), ("wavelength", c_double),
                 ("eps_b", c_double), ("T", c_int), ("tx_angles", POINTER(c_double)), ("M", c_int),
-                ("rx_pos", POINTER(c_double)), ("complex_f", c_int), ("pad", c_int), ("tx_kind", c_int)]
+                ("rx_pos", POINTER(c_double)), ("complex_f", c_int), ("pad", c_int), ("tx_kind", c_int),
+                ("vectorial", c_int)]
 
 
 class SolveOpts(Structure):
@@ -182,10 +183,12 @@ class Cisor:
     """One imaging geometry: tables and workspace on the current CUDA device."""
 
     def __init__(self, n=None, delta=None, tx_angles=None, rx_pos=None, wavelength=1.0, eps_b=1.0, complex_f=False,
-                 pad=0, stream=None, dim=2, tx_kind=0, _handle=None):
+                 pad=0, stream=None, dim=2, tx_kind=0, vectorial=False, _handle=None):
         """2D: tx_angles [T] plane-wave angles, rx_pos [M, 2].  3D (dim=3):
         tx_angles [T, 3] unit propagation directions, rx_pos [M, 3].
-        tx_kind=1 (or "point"): tx_angles holds source positions [T, dim]."""
+        tx_kind=1 (or "point"): tx_angles holds source positions [T, dim].
+        vectorial=True (dim=3): the vectorial model of the appendix; tx_angles is
+        [T, 6] (unit direction, orthogonal unit polarisation) and fields are [T, 3, N]."""
         lib = load()
         self._lib = lib
         self._owned = _handle is None
@@ -194,16 +197,19 @@ class Cisor:
             self.stream = stream
             self.complex_f = bool(complex_f)
             self.dim = int(dim)
+            self.ncomp = 3 if vectorial else 1
             self._read_sizes()
             return
         self.dim = int(dim)
+        self.ncomp = 3 if vectorial else 1
         kind = 1 if tx_kind in (1, "point") else 0
-        per_tx = (self.dim,) if kind == 1 else ((3,) if self.dim == 3 else ())
+        per_tx = (6,) if vectorial else ((self.dim,) if kind == 1 else ((3,) if self.dim == 3 else ()))
         self._ang = np.ascontiguousarray(tx_angles, dtype=np.float64).reshape((-1,) + per_tx)
         self._rx = np.ascontiguousarray(rx_pos, dtype=np.float64).reshape(-1, self.dim)
         g = Geometry(self.dim, int(n), float(delta), float(wavelength), float(eps_b), len(self._ang),
                      self._ang.ctypes.data_as(POINTER(c_double)), len(self._rx),
-                     self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad), kind)
+                     self._rx.ctypes.data_as(POINTER(c_double)), 1 if complex_f else 0, int(pad), kind,
+                     1 if vectorial else 0)
         self._ctx = c_void_p()
         self.stream = _current_stream() if stream is None else stream
         _check(lib.cisor_create(ctypes.byref(self._ctx), ctypes.byref(g), self.stream))
@@ -215,6 +221,7 @@ class Cisor:
         _check(self._lib.cisor_sizes(self._ctx, ctypes.byref(n_), ctypes.byref(P), ctypes.byref(T),
                                      ctypes.byref(M), ctypes.byref(N)))
         self.n, self.P, self.T, self.M, self.N = n_.value, P.value, T.value, M.value, N.value
+        self.Nf = self.N * getattr(self, "ncomp", 1)  # field length per transmitter
 
     def autotune(self, reps=5):
         nt = c_int()
@@ -258,32 +265,32 @@ class Cisor:
         return _check(self._lib.cisor_green_spectrum(self._ctx, ptr(out, self.P ** self.dim)))
 
     def sensing_matrix(self, out):
-        return _check(self._lib.cisor_sensing_matrix(self._ctx, ptr(out, self.M * self.N)))
+        return _check(self._lib.cisor_sensing_matrix(self._ctx, ptr(out, self.M * self.Nf)))
 
     def incident(self, out):
-        return _check(self._lib.cisor_incident(self._ctx, ptr(out, self.T * self.N)))
+        return _check(self._lib.cisor_incident(self._ctx, ptr(out, self.T * self.Nf)))
 
     # ----- operators
     def apply_A(self, f, x, y, adjoint=False):
-        nvec = (x.numel() if hasattr(x, "numel") else x.size) // self.N
-        return _check(self._lib.cisor_apply_A(self._ctx, ptr(f, self.N), ptr(x, nvec * self.N),
-                                              ptr(y, nvec * self.N), 1 if adjoint else 0, nvec))
+        nvec = (x.numel() if hasattr(x, "numel") else x.size) // self.Nf
+        return _check(self._lib.cisor_apply_A(self._ctx, ptr(f, self.N), ptr(x, nvec * self.Nf),
+                                              ptr(y, nvec * self.Nf), 1 if adjoint else 0, nvec))
 
     def sense(self, f, u, Z):
-        return _check(self._lib.cisor_sense(self._ctx, ptr(f, self.N), ptr(u, self.T * self.N),
+        return _check(self._lib.cisor_sense(self._ctx, ptr(f, self.N), ptr(u, self.T * self.Nf),
                                             ptr(Z, self.T * self.M)))
 
     def sense_adjoint(self, f, w, z=None, b=None):
         return _check(self._lib.cisor_sense_adjoint(self._ctx, ptr(f, self.N), ptr(w, self.T * self.M),
-                                                    ptr(z, self.T * self.N), ptr(b, self.T * self.N)))
+                                                    ptr(z, self.T * self.Nf), ptr(b, self.T * self.Nf)))
 
     # ----- solves and gradient
     def forward(self, f, u_in=None, x0=None, u_out=None, y_out=None, tol=1e-4, max_iter=2000, x0_mode=0,
                 check=True):
         opts = SolveOpts(tol, max_iter, x0_mode)
         info = SolveInfo()
-        st = self._lib.cisor_forward(self._ctx, ptr(f, self.N), ptr(u_in, self.T * self.N),
-                                     ptr(x0, self.T * self.N), ptr(u_out, self.T * self.N),
+        st = self._lib.cisor_forward(self._ctx, ptr(f, self.N), ptr(u_in, self.T * self.Nf),
+                                     ptr(x0, self.T * self.Nf), ptr(u_out, self.T * self.Nf),
                                      ptr(y_out, self.T * self.M), ctypes.byref(opts), ctypes.byref(info))
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return st, info
@@ -357,13 +364,14 @@ class Cisor:
 def _geometry(g, keep):
     dim = int(g.get("dim", 2))
     kind = 1 if g.get("tx_kind", 0) in (1, "point") else 0
-    per_tx = (dim,) if kind == 1 else ((3,) if dim == 3 else ())
+    vec = 1 if g.get("vectorial") else 0
+    per_tx = (6,) if vec else ((dim,) if kind == 1 else ((3,) if dim == 3 else ()))
     ang = np.ascontiguousarray(g["tx_angles"], dtype=np.float64).reshape((-1,) + per_tx)
     rx = np.ascontiguousarray(g["rx_pos"], dtype=np.float64).reshape(-1, dim)
     keep += [ang, rx]
     return Geometry(dim, int(g["n"]), float(g["delta"]), float(g.get("wavelength", 1.0)), float(g.get("eps_b", 1.0)),
                     len(ang), ang.ctypes.data_as(POINTER(c_double)), len(rx), rx.ctypes.data_as(POINTER(c_double)),
-                    1 if g.get("complex_f") else 0, int(g.get("pad", 0)), kind)
+                    1 if g.get("complex_f") else 0, int(g.get("pad", 0)), kind, vec)
 
 
 class Batch:
@@ -383,7 +391,7 @@ class Batch:
             h = c_void_p()
             _check(lib.cisor_batch_context(self._b, i, ctypes.byref(h)))
             self.problems.append(Cisor(_handle=h, stream=self.stream, complex_f=g.get("complex_f", False),
-                                       dim=g.get("dim", 2)))
+                                       dim=g.get("dim", 2), vectorial=bool(g.get("vectorial", False))))
 
     def close(self):
         if getattr(self, "_b", None):
@@ -404,7 +412,7 @@ class Batch:
         opts = SolveOpts(tol, max_iter, x0_mode)
         infos = (SolveInfo * len(ps))()
         fp = self._ptrs(f, [p.N for p in ps])
-        up = self._ptrs(u_out, [p.T * p.N for p in ps]) if u_out is not None else None
+        up = self._ptrs(u_out, [p.T * p.Nf for p in ps]) if u_out is not None else None
         st = self._lib.cisor_batch_forward(self._b, fp, up, ctypes.byref(opts), infos)
         _check(st, () if check else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
         return st, list(infos)

@@ -100,7 +100,7 @@ static bool solve_ok(cisor_status s) {
 // (the data): forward solve into c->u (kept: the fields are the checkpoint the
 // backward half needs), Z, w = Z - y and D.
 static cisor_status data_core(cisor_ctx* c, const cisor_solve_opts* o, double* D, cisor_solve_info* li) {
-  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
   if (o->x0_mode != 2 || !c->have_u) CISOR_CUDA(cudaMemcpyAsync(c->u, c->u_in, vb, cudaMemcpyDeviceToDevice, c->stream));
   int nb1 = 0;
   c->have_w = 0;
@@ -122,7 +122,7 @@ static cisor_status data_core(cisor_ctx* c, const cisor_solve_opts* o, double* D
 // zstep = s - gamma g.  Needs data_core's u and w.
 static cisor_status adjoint_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s,
                                  float2* zstep, cisor_solve_info* li) {
-  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
   CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
   if (o->x0_mode != 2 || !c->have_v) CISOR_CUDA(cudaMemsetAsync(c->vadj, 0, vb, c->stream));
   int nb2 = 0;
@@ -131,17 +131,21 @@ static cisor_status adjoint_core(cisor_ctx* c, const cisor_solve_opts* o, double
   if (!solve_ok(s2)) return s2;
   c->have_v = 1;
   li->n_not_converged += nb2;
-  ConvOp op{};
-  op.adjoint = 1;
-  op.mul_f = 0;
-  op.prologue = PRO_COPY;
-  op.src = c->vadj;
-  op.epilogue = EPI_CONV_ADD;
-  op.aux = c->z;
-  op.out = c->gz;
-  op.f = c->f;
-  op.ntx = c->T;
-  CISOR_TRY(conv_pass(c, op));
+  if (c->ncomp == 3) {
+    CISOR_TRY(vec_gz(c));  // z + conv_{G^H}(v + D v / k^2)
+  } else {
+    ConvOp op{};
+    op.adjoint = 1;
+    op.mul_f = 0;
+    op.prologue = PRO_COPY;
+    op.src = c->vadj;
+    op.epilogue = EPI_CONV_ADD;
+    op.aux = c->z;
+    op.out = c->gz;
+    op.f = c->f;
+    op.ntx = c->T;
+    CISOR_TRY(conv_pass(c, op));
+  }
   CISOR_TRY(grad_assemble(c, c->u, c->gz, s, gamma, c->grad, zstep, c->T));
   return s2;
 }
@@ -165,7 +169,7 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -203,6 +207,21 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
               g->wavelength, g->eps_b);
     return CISOR_ERR_INVALID_ARG;
   }
+  if (g->vectorial && (g->dim != 3 || g->tx_kind != 0 || g->eps_b != 1.0 || g->n > 64)) {
+    set_error("the vectorial model needs dim 3, polarised plane waves (tx_kind 0), eps_b = 1 and n <= 64");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (g->vectorial) {  // [T, 6]: unit direction d_t, unit polarisation p_t, p_t . d_t = 0
+    for (int t = 0; t < g->T; ++t) {
+      const double* q = g->tx_angles + 6 * t;
+      const double dd = q[0] * q[0] + q[1] * q[1] + q[2] * q[2], pp = q[3] * q[3] + q[4] * q[4] + q[5] * q[5];
+      const double dp = q[0] * q[3] + q[1] * q[4] + q[2] * q[5];
+      if (fabs(dd - 1.0) > 1e-6 || fabs(pp - 1.0) > 1e-6 || fabs(dp) > 1e-6) {
+        set_error("transmitter %d: direction and polarisation must be orthogonal unit vectors", t);
+        return CISOR_ERR_INVALID_ARG;
+      }
+    }
+  }
   if (g->tx_kind != 0 && g->tx_kind != 1) {
     set_error("tx_kind must be 0 (plane waves) or 1 (point sources), got %d", g->tx_kind);
     return CISOR_ERR_INVALID_ARG;
@@ -239,6 +258,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->M = g->M;
   c->complex_f = g->complex_f ? 1 : 0;
   c->N = (long long)g->n * g->n * (g->dim == 3 ? g->n : 1);
+  c->ncomp = g->vectorial ? 3 : 1;
+  c->Nf = c->N * c->ncomp;
   c->delta = g->delta;
   c->wavelength = g->wavelength;
   c->eps_b = g->eps_b;
@@ -246,7 +267,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->kb = c->k * sqrt(g->eps_b);
   const int d = g->dim;
   c->tx_kind = g->tx_kind;
-  c->tx_angles.assign(g->tx_angles, g->tx_angles + (g->tx_kind == 1 ? (size_t)d * g->T : (d == 3 ? 3 * g->T : g->T)));
+  const size_t per_tx = g->vectorial ? 6 : (g->tx_kind == 1 ? (size_t)d : (d == 3 ? 3 : 1));
+  c->tx_angles.assign(g->tx_angles, g->tx_angles + per_tx * g->T);
   c->rx_pos.assign(g->rx_pos, g->rx_pos + (size_t)d * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
@@ -256,7 +278,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     // split-K of the forward sensing GEMM: about 4 CTAs per SM, chunks of >= 256 pixels
     const int tiles = sense_tiles(c->M, c->T);
     int ks = (4 * 152 + tiles - 1) / tiles;
-    const int kmax = (int)((c->N + 255) / 256);
+    const int kmax = (int)((c->Nf + 255) / 256);
     c->ksplit = ks < 1 ? 1 : (ks > kmax ? kmax : ks);
   }
   cisor_status st = CISOR_OK;
@@ -276,16 +298,16 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(cuda_fail(e, "stream/event setup", __FILE__, __LINE__));
   }
-  const size_t TN = (size_t)c->T * c->N * sizeof(float2);
+  const size_t TN = (size_t)c->T * c->Nf * sizeof(float2);
   const size_t Nb = (size_t)c->N * sizeof(float2);
   const size_t TM = (size_t)c->T * c->M * sizeof(float2);
   const size_t Pd = (size_t)P * P * (d == 3 ? P : 1);
   ALLOC(c->ghat, sizeof(float2) * Pd);
   ALLOC(c->tw, sizeof(float2) * P);
   ALLOC(c->twst, sizeof(float2) * 2 * 512);
-  ALLOC(c->H, (size_t)c->M * c->N * sizeof(float2));
+  ALLOC(c->H, (size_t)c->M * c->Nf * sizeof(float2));
   ALLOC(c->u_in, TN);
-  ALLOC(c->R, (size_t)c->T * c->rtstride * sizeof(float2));
+  ALLOC(c->R, (size_t)c->T * c->ncomp * c->rtstride * sizeof(float2));
   ALLOC(c->r, TN);
   ALLOC(c->rhat, TN);
   ALLOC(c->p, TN);
@@ -305,7 +327,8 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->w, TM);
   ALLOC(c->yobs, TM);
   ALLOC(c->sense_part, TM * c->ksplit);
-  ALLOC(c->part, sizeof(float) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk);
+  ALLOC(c->part, sizeof(float) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk * c->ncomp);
+  if (c->ncomp == 3) ALLOC(c->vbuf, TN);
   ALLOC(c->scal, sizeof(double) * 2 * SC_STRIDE * (size_t)c->T);
   ALLOC(c->active, sizeof(int) * c->T);
   ALLOC(c->iters, sizeof(int) * c->T);
@@ -372,7 +395,7 @@ cisor_status cisor_sensing_matrix(cisor_ctx* c, void* out) {
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  CISOR_TRY(call.out(out, c->H, sizeof(float2) * (size_t)c->M * c->N));
+  CISOR_TRY(call.out(out, c->H, sizeof(float2) * (size_t)c->M * c->Nf));
   return call.leave();
 }
 
@@ -383,8 +406,32 @@ cisor_status cisor_incident(cisor_ctx* c, void* out) {
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  CISOR_TRY(call.out(out, c->u_in, sizeof(float2) * (size_t)c->T * c->N));
+  CISOR_TRY(call.out(out, c->u_in, sizeof(float2) * (size_t)c->T * c->Nf));
   return call.leave();
+}
+
+// y = A x (or A^H x) for nvec fields, no dot products
+static cisor_status matvec_once(cisor_ctx* c, int adjoint, int nvec, const float2* x, float2* y) {
+  if (c->ncomp == 3) {
+    VecOp vo{};
+    vo.adjoint = adjoint ? 1 : 0;
+    vo.epilogue = EPI_MATVEC;
+    vo.x = x;
+    vo.out = y;
+    vo.ntx = nvec;
+    return vec_matvec(c, vo);
+  }
+  ConvOp op{};
+  op.adjoint = adjoint ? 1 : 0;
+  op.mul_f = 1;
+  op.prologue = PRO_COPY;
+  op.src = x;
+  op.epilogue = EPI_MATVEC;
+  op.esrc = x;
+  op.out = y;
+  op.f = c->f;
+  op.ntx = nvec;
+  return conv_pass(c, op);
 }
 
 cisor_status cisor_apply_A(cisor_ctx* c, const void* f, const void* x, void* y, int adjoint, int nvec) {
@@ -394,20 +441,10 @@ cisor_status cisor_apply_A(cisor_ctx* c, const void* f, const void* x, void* y, 
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  const size_t vb = sizeof(float2) * (size_t)nvec * c->N;
+  const size_t vb = sizeof(float2) * (size_t)nvec * c->Nf;
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   CISOR_TRY(call.in(c->s, x, vb));
-  ConvOp op{};
-  op.adjoint = adjoint ? 1 : 0;
-  op.mul_f = 1;
-  op.prologue = PRO_COPY;
-  op.src = c->s;
-  op.epilogue = EPI_MATVEC;
-  op.esrc = c->s;
-  op.out = c->tv;
-  op.f = c->f;
-  op.ntx = nvec;
-  CISOR_TRY(conv_pass(c, op));
+  CISOR_TRY(matvec_once(c, adjoint, nvec, c->s, c->tv));
   CISOR_TRY(call.out(y, c->tv, vb));
   return call.leave();
 }
@@ -425,7 +462,7 @@ cisor_status cisor_forward(cisor_ctx* c, const void* f, const void* u_in, const 
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   const float2* b = c->u_in;
   if (u_in) {
@@ -462,7 +499,7 @@ cisor_status cisor_sense(cisor_ctx* c, const void* f, const void* u, void* Z_out
   Call call(c);
   CISOR_TRY(call.enter());
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
-  CISOR_TRY(call.in(c->s, u, sizeof(float2) * (size_t)c->T * c->N));
+  CISOR_TRY(call.in(c->s, u, sizeof(float2) * (size_t)c->T * c->Nf));
   CISOR_TRY(sense_forward(c, c->f, c->s, c->Y, c->T));
   CISOR_TRY(call.out(Z_out, c->Y, sizeof(float2) * (size_t)c->T * c->M));
   return call.leave();
@@ -478,7 +515,7 @@ cisor_status cisor_sense_adjoint(cisor_ctx* c, const void* f, const void* w, voi
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   CISOR_TRY(call.in(c->w, w, sizeof(float2) * (size_t)c->T * c->M));
   CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
-  const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+  const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
   CISOR_TRY(call.out(z_out, c->z, vb));
   CISOR_TRY(call.out(b_out, c->b, vb));
   return call.leave();
@@ -702,17 +739,8 @@ cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   }
   Call call(c);
   CISOR_TRY(call.enter());
-  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->Nf, cudaMemcpyDeviceToDevice, c->stream));
   CISOR_CUDA(cudaMemsetAsync(c->f, 0, sizeof(float2) * c->N, c->stream));
-  ConvOp op{};
-  op.mul_f = 1;
-  op.prologue = PRO_COPY;
-  op.src = c->s;
-  op.epilogue = EPI_MATVEC;
-  op.esrc = c->s;
-  op.out = c->tv;
-  op.f = c->f;
-  op.ntx = c->T;
   cudaEvent_t e0, e1;
   CISOR_CUDA(cudaEventCreate(&e0));
   CISOR_CUDA(cudaEventCreate(&e1));
@@ -722,9 +750,9 @@ cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   cisor_status st = CISOR_OK;
   for (int v = 0; v < 2 && st == CISOR_OK; ++v) {
     c->cols_nt = variants[v];
-    st = conv_pass(c, op);  // warm-up
+    st = matvec_once(c, 0, c->T, c->s, c->tv);  // warm-up
     CISOR_CUDA(cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < reps && st == CISOR_OK; ++i) st = conv_pass(c, op);
+    for (int i = 0; i < reps && st == CISOR_OK; ++i) st = matvec_once(c, 0, c->T, c->s, c->tv);
     CISOR_CUDA(cudaEventRecord(e1, c->stream));
     CISOR_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -764,24 +792,14 @@ cisor_status cisor_time_matvec(cisor_ctx* c, const void* f, int adjoint, int rep
   Call call(c);
   CISOR_TRY(call.enter());
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
-  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->N, cudaMemcpyDeviceToDevice, c->stream));
-  ConvOp op{};
-  op.adjoint = adjoint ? 1 : 0;
-  op.mul_f = 1;
-  op.prologue = PRO_COPY;
-  op.src = c->s;
-  op.epilogue = EPI_MATVEC;
-  op.esrc = c->s;
-  op.out = c->tv;
-  op.f = c->f;
-  op.ntx = c->T;
-  CISOR_TRY(conv_pass(c, op));
+  CISOR_CUDA(cudaMemcpyAsync(c->s, c->u_in, sizeof(float2) * (size_t)c->T * c->Nf, cudaMemcpyDeviceToDevice, c->stream));
+  CISOR_TRY(matvec_once(c, adjoint, c->T, c->s, c->tv));
   cudaEvent_t e0, e1;
   CISOR_CUDA(cudaEventCreate(&e0));
   CISOR_CUDA(cudaEventCreate(&e1));
   CISOR_CUDA(cudaEventRecord(e0, c->stream));
   cisor_status st = CISOR_OK;
-  for (int i = 0; i < reps && st == CISOR_OK; ++i) st = conv_pass(c, op);
+  for (int i = 0; i < reps && st == CISOR_OK; ++i) st = matvec_once(c, adjoint, c->T, c->s, c->tv);
   CISOR_CUDA(cudaEventRecord(e1, c->stream));
   CISOR_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;

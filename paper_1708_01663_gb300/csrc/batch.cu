@@ -178,7 +178,7 @@ cisor_status cisor_batch_forward(cisor_batch* b, const void* const* f, void* con
   std::vector<const float2*> rhs(np);
   for (int i = 0; i < np; ++i) {
     cisor_ctx* c = b->ctx[i];
-    const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+    const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
     CISOR_CUDA(cudaMemcpyAsync(c->f, f[i], sizeof(float2) * c->N, cudaMemcpyDefault, c->stream));
     if (o->x0_mode == 0 || !c->have_u)
       CISOR_CUDA(cudaMemcpyAsync(c->u, c->u_in, vb, cudaMemcpyDeviceToDevice, c->stream));
@@ -193,7 +193,7 @@ cisor_status cisor_batch_forward(cisor_batch* b, const void* const* f, void* con
     c->have_u = 1;
     if (u_out && u_out[i]) {
       host_out |= is_host(u_out[i]);
-      CISOR_CUDA(cudaMemcpyAsync(u_out[i], c->u, sizeof(float2) * (size_t)c->T * c->N, cudaMemcpyDefault,
+      CISOR_CUDA(cudaMemcpyAsync(u_out[i], c->u, sizeof(float2) * (size_t)c->T * c->Nf, cudaMemcpyDefault,
                                  c->stream));
     }
     if (info) fill_info(&info[i], st[i], nullptr);
@@ -219,7 +219,7 @@ cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* 
   std::vector<const float2*> rhs(np);
   for (int i = 0; i < np; ++i) {
     cisor_ctx* c = b->ctx[i];
-    const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+    const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
     CISOR_CUDA(cudaMemcpyAsync(c->f, f[i], sizeof(float2) * c->N, cudaMemcpyDefault, c->stream));
     CISOR_CUDA(cudaMemcpyAsync(c->yobs, y[i], sizeof(float2) * (size_t)c->T * c->M, cudaMemcpyDefault, c->stream));
     if (o->x0_mode == 0 || !c->have_u)
@@ -231,7 +231,7 @@ cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* 
   if (!solve_ok(s1)) return s1;
   for (int i = 0; i < np; ++i) {
     cisor_ctx* c = b->ctx[i];
-    const size_t vb = sizeof(float2) * (size_t)c->T * c->N;
+    const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
     c->have_u = 1;
     CISOR_TRY(residual_and_D(c, c->f, c->u, c->yobs, c->Y, c->w, c->T));
     CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));

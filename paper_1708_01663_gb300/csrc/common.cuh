@@ -88,6 +88,8 @@ struct cisor_ctx {
   // geometry
   int dim, n, P, T, M, complex_f;
   long long N;
+  int ncomp;              // field components: 1 (scalar), 3 (vectorial model of the appendix)
+  long long Nf;           // field length per transmitter: ncomp * N
   int nrows;              // x rows per field: n (2D), n^2 (3D)
   long long rslab;        // R offset between z slabs (3D: P^2)
   long long rtstride;     // R elements per transmitter
@@ -125,6 +127,7 @@ struct cisor_ctx {
   // TV workspace (d dual components x N floats per plane, up to 2 planes)
   float *tv_z, *tv_r0, *tv_r1, *tv_p;
   float *tva0, *tva1;  // anisotropic TV: (2d + 1) auxiliary images per plane, ping-pong
+  float2* vbuf;        // vectorial model: conv output / grad-div pre-pass [T, 3, N]
   // graphs of a chunk of BiCGSTAB iterations
   cudaGraphExec_t graph[2];
   int graph_ntx[2];
@@ -179,6 +182,8 @@ struct ConvOp {
   const double* scal;     // per-transmitter scalars (alpha, beta, omega)
   float* part;            // dot partials [T, nblk, DOT_SLOTS] float2
   int ntx;
+  int tx_div;             // transforms per transmitter (3: the field components of the vectorial
+                          // model run as consecutive transforms; 0 or 1: one)
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
 // EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);
@@ -212,6 +217,26 @@ struct MultiSolve {
 };
 cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2* const* b, double tol, int max_iter,
                          MultiSolve& ms, SolveStat* st);
+
+// vector.cu: the vectorial model (appendix).  Matvec over [ntx, 3, N] fields:
+// A x = x - C - D C / k^2 (C = conv_G(f x)) or A^H x = x - conj(f) conv_{G^H}(x + D x / k^2),
+// with the epilogue (MATVEC / RESID, dot slots) of a ConvOp; partials land in
+// [T][3 nblk][DOT_SLOTS].
+struct VecOp {
+  int adjoint, epilogue;  // EPI_MATVEC or EPI_RESID
+  const float2* x;        // input (and the x of A x)
+  const float2* aux;      // b of EPI_RESID, dot operand
+  float2* out;
+  float2* out2;
+  int dot_a[DOT_SLOTS], dot_b[DOT_SLOTS];
+  const int* active;
+  int ntx;
+};
+cisor_status vec_matvec(cisor_ctx* c, const VecOp& op);
+cisor_status vec_pupdate(cisor_ctx* c, int ntx);   // p = r + beta (p - omega v), per transmitter
+cisor_status vec_axpy(cisor_ctx* c, int ntx);      // s = r - alpha v
+cisor_status vec_gz(cisor_ctx* c);                 // gz = z + conv_{G^H}(v + D v / k^2)
+cisor_status vec_tables(cisor_ctx* c, const double* d_tx, const double* d_rx);  // H~, E_in
 
 // sense.cu
 int sense_tiles(int M, int T);  // CTA tiles of the forward sensing GEMM (before split-K)

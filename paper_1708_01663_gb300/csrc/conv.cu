@@ -22,6 +22,7 @@
 // inverse-only mode along y (P inputs, n kept); rows_inv.
 // ghat is pre-scaled by 1/P^d, so the inverse transforms are unnormalised.
 #include "common.cuh"
+#include "dots.cuh"
 #include "fft.cuh"
 #include "regfft.cuh"
 
@@ -70,7 +71,8 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   __shared__ float2 tw[TwTable<P, false>::SIZE];
   __shared__ float2 buf[C::RB * C::PP];
   const int tx = blockIdx.y;
-  if (op.active && !op.active[tx]) return;
+  const int txs = op.tx_div > 1 ? tx / op.tx_div : tx;  // transmitter of this transform
+  if (op.active && !op.active[txs]) return;
   const int n = geo.n;
   const int lt = threadIdx.x % C::NTF, row = threadIdx.x / C::NTF;
   const int iy = blockIdx.x * C::RB + row;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 256) tw[i] = tw_g[i];
   float2 alpha = make_float2(0.f, 0.f), beta = alpha, omega = alpha;
   if (PRO != PRO_COPY) {
-    const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)tx * SC_STRIDE;
+    const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)txs * SC_STRIDE;
     alpha = z_to_c(sc[SC_ALPHA]);
     beta = z_to_c(sc[SC_BETA]);
     omega = z_to_c(sc[SC_OMEGA]);
@@ -136,6 +138,7 @@ enum { COL_G = 0, COL_FWD = 1, COL_INV = 2 };
 struct ColGeo {
   int n, cps;  // column blocks per slab (P / W)
   long long es, slab, tstride;
+  int tx_div;
 };
 
 // D3 = false (2D) fixes es = P and a single slab at compile time.
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
   constexpr int W = C::template Col<NT>::W;
   __shared__ float2 buf[P * W];
   const int tx = blockIdx.y;
-  if (active && !active[tx]) return;
+  if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
   const int w = threadIdx.x % W, lt = threadIdx.x / W;
   const int j = D3 ? blockIdx.x / geo.cps : 0;
@@ -212,42 +215,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
     }
 }
 
-__device__ __forceinline__ float2 pick(int code, float2 y, float2 s, float2 a) {
-  return code == OP_Y ? y : (code == OP_SRC ? s : a);
-}
-
-// Block-wide sum of three complex FP32 partials: warp shuffles, then the
-// per-warp sums pairwise in shared memory (all FP32), written to part.
-template <int NT>
-__device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], float2* out) {
-  __shared__ float red[2 * DOT_SLOTS][NT / 32];
-  float v[2 * DOT_SLOTS];
-#pragma unroll
-  for (int s = 0; s < DOT_SLOTS; ++s) {
-    v[2 * s] = acc[s].x;
-    v[2 * s + 1] = acc[s].y;
-  }
-#pragma unroll
-  for (int k = 0; k < 2 * DOT_SLOTS; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 2 * DOT_SLOTS; ++k) red[k][wid] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < 2 * DOT_SLOTS) {
-    float* r = red[threadIdx.x];
-#pragma unroll
-    for (int w = NT / 64; w > 0; w >>= 1)
-#pragma unroll
-      for (int i = 0; i < w; ++i) r[i] += r[i + w];
-    reinterpret_cast<float*>(out)[threadIdx.x] = r[0];
-  }
-}
-
 template <int P, int EPI>
 __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const float2* __restrict__ tw_g,
                                                      const float2* __restrict__ R, const RowGeo geo, int nblk) {
@@ -256,7 +223,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   __shared__ float2 tw[TwTable<P, true>::SIZE];
   __shared__ float2 buf[C::RB * C::PP];
   const int tx = blockIdx.y;
-  if (op.active && !op.active[tx]) return;
+  if (op.active && !op.active[op.tx_div > 1 ? tx / op.tx_div : tx]) return;
   const int n = geo.n;
   const int lt = threadIdx.x % C::NTF, row = threadIdx.x / C::NTF;
   const int iy = blockIdx.x * C::RB + row;
@@ -330,7 +297,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
 template <int P, int MODE, bool ADJ, int NT>
 static void launch_cols(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
   constexpr int W = ConvCfg<P>::template Col<NT>::W;
-  const ColGeo geo{c->n, P / W, es, slab, c->rtstride};
+  const ColGeo geo{c->n, P / W, es, slab, c->rtstride, op.tx_div};
   dim3 g((P / W) * nslab, op.ntx);
   if constexpr (P <= 256) {  // 3D grids use P <= 256
     if (c->dim == 3) {

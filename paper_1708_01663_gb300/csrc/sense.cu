@@ -28,9 +28,15 @@ constexpr int GK = 16;   // reduction tile
 
 int sense_tiles(int M, int T) { return ((M + GM - 1) / GM) * ((T + GT - 1) / GT); }
 
+// N is the reduction length (the field length: pixels x components); f repeats with period NP (pixels).
+__device__ __forceinline__ long long fperiod(long long k, long long NP) {
+  while (k >= NP) k -= NP;
+  return k;
+}
+
 __global__ void __launch_bounds__(256, 2) sense_fwd_kernel(const float2* __restrict__ H, const float2* __restrict__ f,
                                                         const float2* __restrict__ u, float2* __restrict__ part, int T,
-                                                        int M, long long N, long long chunk) {
+                                                        int M, long long N, long long chunk, long long NP) {
   __shared__ float2 Hs[2][GK][GM + 1];
   __shared__ float2 Qs[2][GK][GT + 1];
   const int m0 = blockIdx.x * GM, t0 = blockIdx.y * GT, ks = blockIdx.z;
@@ -51,7 +57,7 @@ __global__ void __launch_bounds__(256, 2) sense_fwd_kernel(const float2* __restr
       const int e = tid + 256 * q, kk = e & (GK - 1), tt = e >> 4;
       const long long k = k0 + kk;
       const int t = t0 + tt;
-      qr[q] = (k < ke && t < T) ? c_mul(f[k], u[(long long)t * N + k]) : make_float2(0.f, 0.f);
+      qr[q] = (k < ke && t < T) ? c_mul(f[fperiod(k, NP)], u[(long long)t * N + k]) : make_float2(0.f, 0.f);
     }
   };
   auto stash = [&](int buf) {
@@ -160,7 +166,8 @@ __device__ __forceinline__ void adj_load(const float2* __restrict__ H, const flo
 
 __global__ void __launch_bounds__(256, 2) sense_adj_kernel(const float2* __restrict__ H, const float2* __restrict__ w,
                                                         const float2* __restrict__ f, float2* __restrict__ z,
-                                                        float2* __restrict__ b, int T, int M, long long N) {
+                                                        float2* __restrict__ b, int T, int M, long long N,
+                                                        long long NP) {
   __shared__ float2 Hs[2][GK][GM];
   __shared__ float2 Ws[2][GK][GT + 1];
   const long long n0 = (long long)blockIdx.x * GM;
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(256, 2) sense_adj_kernel(const float2* __restr
       if (t < T && n < N) {
         const long long idx = (long long)t * N + n;
         if (z) z[idx] = acc[i][j];
-        if (b) b[idx] = c_cjmul(f[n], acc[i][j]);
+        if (b) b[idx] = c_cjmul(f[fperiod(n, NP)], acc[i][j]);
       }
     }
 }
@@ -249,10 +256,10 @@ cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, doubl
 }
 
 cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Z, int ntx) {
-  const long long chunk = ((c->N + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
-  const int ks = (int)((c->N + chunk - 1) / chunk);
+  const long long chunk = ((c->Nf + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
+  const int ks = (int)((c->Nf + chunk - 1) / chunk);
   dim3 g((c->M + GM - 1) / GM, (ntx + GT - 1) / GT, ks);
-  sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->N, chunk);
+  sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->Nf, chunk, c->N);
   CISOR_CUDA(cudaGetLastError());
   const int tm = ntx * c->M;
   sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, nullptr, Z, nullptr,
@@ -264,10 +271,10 @@ cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float
 
 cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, const float2* y, float2* Z, float2* w,
                             int ntx) {
-  const long long chunk = ((c->N + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
-  const int ks = (int)((c->N + chunk - 1) / chunk);
+  const long long chunk = ((c->Nf + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
+  const int ks = (int)((c->Nf + chunk - 1) / chunk);
   dim3 g((c->M + GM - 1) / GM, (ntx + GT - 1) / GT, ks);
-  sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->N, chunk);
+  sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->Nf, chunk, c->N);
   CISOR_CUDA(cudaGetLastError());
   CISOR_CUDA(cudaMemsetAsync(c->dsum, 0, sizeof(double), c->stream));
   const int tm = ntx * c->M;
@@ -279,8 +286,8 @@ cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, cons
 }
 
 cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx) {
-  dim3 g((unsigned)((c->N + GM - 1) / GM), (ntx + GT - 1) / GT);
-  sense_adj_kernel<<<g, 256, 0, c->stream>>>(c->H, w, f, z, b, ntx, c->M, c->N);
+  dim3 g((unsigned)((c->Nf + GM - 1) / GM), (ntx + GT - 1) / GT);
+  sense_adj_kernel<<<g, 256, 0, c->stream>>>(c->H, w, f, z, b, ntx, c->M, c->Nf, c->N);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return CISOR_OK;
@@ -288,8 +295,9 @@ cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float
 
 cisor_status grad_assemble(cisor_ctx* c, const float2* u, const float2* gz, const float2* s, double gamma,
                            float2* grad, float2* zstep, int ntx) {
-  grad_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(u, gz, ntx, c->N, s, (float)gamma, c->complex_f,
-                                                                     grad, zstep);
+  // the components of the vectorial model are consecutive [N] blocks of a transmitter: sum them too
+  grad_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(u, gz, ntx * c->ncomp, c->N, s, (float)gamma,
+                                                                     c->complex_f, grad, zstep);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return CISOR_OK;

@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int nrows, int 
 }
 
 static cisor_status scalar_step(cisor_ctx* c, int mode, int ntx) {
-  bicg_scalar_kernel<<<ntx, 32, 0, c->stream>>>(mode, c->nblk, c->part, c->scal, c->active, c->iters, c->txflag,
-                                               c->sparams);
+  bicg_scalar_kernel<<<ntx, 32, 0, c->stream>>>(mode, c->nblk * c->ncomp, c->part, c->scal, c->active, c->iters,
+                                               c->txflag, c->sparams);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return CISOR_OK;
@@ -229,6 +229,21 @@ static ConvOp base_op(cisor_ctx* c, int adjoint, int ntx) {
 
 // r = b - A x ; rhat = r ; partials <b,b> (slot 0) and <r,r> (slot 2)
 static cisor_status residual_pass(cisor_ctx* c, int adjoint, const float2* b, const float2* x, int ntx) {
+  if (c->ncomp == 3) {
+    VecOp vo{};
+    vo.adjoint = adjoint;
+    vo.epilogue = EPI_RESID;
+    vo.x = x;
+    vo.aux = b;
+    vo.out = c->r;
+    vo.out2 = c->rhat;
+    vo.dot_a[0] = OP_AUX;
+    vo.dot_b[0] = OP_AUX;
+    vo.dot_a[2] = OP_Y;
+    vo.dot_b[2] = OP_Y;
+    vo.ntx = ntx;
+    return vec_matvec(c, vo);
+  }
   ConvOp op = base_op(c, adjoint, ntx);
   op.prologue = PRO_COPY;
   op.src = x;
@@ -244,7 +259,52 @@ static cisor_status residual_pass(cisor_ctx* c, int adjoint, const float2* b, co
   return conv_pass(c, op);
 }
 
+// x += alpha p + omega s ; r = s - omega t ; <rhat, r>, <r, r>, then rho', beta, convergence
+static cisor_status update_step(cisor_ctx* c, float2* x, int ntx) {
+  const int RB = conv_rows_per_block(c->P);
+  dim3 g(c->nblk * c->ncomp, ntx);
+  bicg_update_kernel<<<g, 256, 0, c->stream>>>(c->n, c->nrows * c->ncomp, RB, c->nblk * c->ncomp, c->active, c->scal,
+                                               x, c->p, c->s, c->tv, c->r, c->rhat, c->part);
+  CISOR_CUDA(cudaGetLastError());
+  c->launches += 1;
+  return scalar_step(c, SCM_RHO, ntx);
+}
+
+// The vectorial model: the same recurrence with the vector updates in their
+// own kernels around the stencil-plus-convolution matvec.
+static cisor_status enqueue_iteration_vec(cisor_ctx* c, int adjoint, float2* x, int ntx) {
+  CISOR_TRY(vec_pupdate(c, ntx));
+  VecOp op{};
+  op.adjoint = adjoint;
+  op.epilogue = EPI_MATVEC;
+  op.x = c->p;
+  op.aux = c->rhat;
+  op.out = c->v;
+  op.dot_a[0] = OP_AUX;
+  op.dot_b[0] = OP_Y;
+  op.active = c->active;
+  op.ntx = ntx;
+  CISOR_TRY(vec_matvec(c, op));
+  CISOR_TRY(scalar_step(c, SCM_ALPHA, ntx));
+  CISOR_TRY(vec_axpy(c, ntx));
+  VecOp op2{};
+  op2.adjoint = adjoint;
+  op2.epilogue = EPI_MATVEC;
+  op2.x = c->s;
+  op2.out = c->tv;
+  op2.dot_a[1] = OP_Y;
+  op2.dot_b[1] = OP_SRC;
+  op2.dot_a[2] = OP_Y;
+  op2.dot_b[2] = OP_Y;
+  op2.active = c->active;
+  op2.ntx = ntx;
+  CISOR_TRY(vec_matvec(c, op2));
+  CISOR_TRY(scalar_step(c, SCM_OMEGA, ntx));
+  return update_step(c, x, ntx);
+}
+
 static cisor_status enqueue_iteration(cisor_ctx* c, int adjoint, float2* x, int ntx) {
+  if (c->ncomp == 3) return enqueue_iteration_vec(c, adjoint, x, ntx);
   // p = r + beta (p - omega v) ; v = A p ; <rhat, v>
   ConvOp op = base_op(c, adjoint, ntx);
   op.active = c->active;
@@ -276,13 +336,7 @@ static cisor_status enqueue_iteration(cisor_ctx* c, int adjoint, float2* x, int 
   op2.dot_b[2] = OP_Y;
   CISOR_TRY(conv_pass(c, op2));
   CISOR_TRY(scalar_step(c, SCM_OMEGA, ntx));
-  const int RB = conv_rows_per_block(c->P);
-  dim3 g(c->nblk, ntx);
-  bicg_update_kernel<<<g, 256, 0, c->stream>>>(c->n, c->nrows, RB, c->nblk, c->active, c->scal, x, c->p, c->s, c->tv, c->r,
-                                               c->rhat, c->part);
-  CISOR_CUDA(cudaGetLastError());
-  c->launches += 1;
-  return scalar_step(c, SCM_RHO, ntx);
+  return update_step(c, x, ntx);
 }
 
 static cisor_status get_graph(cisor_ctx* c, int adjoint, float2* x, int ntx, cudaGraphExec_t* out) {
@@ -329,7 +383,7 @@ static cisor_status read_active(cisor_ctx* c, int ntx, int* n_active) {
 // runs the INIT scalar step (all on c->stream).
 static cisor_status init_solve(cisor_ctx* c, int adjoint, const float2* b, float2* x, int ntx, double tol,
                                int max_iter) {
-  const size_t vb = sizeof(float2) * (size_t)ntx * c->N;
+  const size_t vb = sizeof(float2) * (size_t)ntx * c->Nf;
   // pageable source: the copy is staged before cudaMemcpyAsync returns, so the stack array may go
   const double hp[2] = {tol, (double)max_iter};
   CISOR_CUDA(cudaMemcpyAsync(c->sparams, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream));

@@ -75,6 +75,8 @@ extern "C" cisor_status cisor_apply_A_static(const void* ghat_scaled, const void
   c.R = reinterpret_cast<float2*>(base) + kStaticTwiddleFloats2;
   c.ghat = reinterpret_cast<float2*>(const_cast<void*>(ghat_scaled));
   c.dim = 2;
+  c.ncomp = 1;
+  c.Nf = c.N;
   c.cols_nt = 512;
   conv_geometry(&c);
   CISOR_TRY(make_stage_twiddles(&c));

@@ -332,13 +332,17 @@ cisor_status build_tables(cisor_ctx* c) {
   }
   long long MN = (long long)c->M * c->N;
   long long TN = (long long)c->T * c->N;
-  if (d == 3)
+  if (c->ncomp == 3) {  // vectorial model: dyadic sensing row and polarised plane waves
+    CISOR_TRY(vec_tables(c, d_ang, d_rx));
+  } else if (d == 3)
     sensing3d_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
   else
     sensing_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
   CISOR_CUDA(cudaGetLastError());
   const unsigned gT = (unsigned)((TN + 255) / 256);
-  if (c->tx_kind == 1)
+  if (c->ncomp == 3)
+    ;  // incident fields written by vec_tables
+  else if (c->tx_kind == 1)
     point_source_kernel<<<gT, 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, d, c->delta, c->kb);
   else if (d == 3)
     plane_wave3d_kernel<<<gT, 256, 0, c->stream>>>(c->u_in, d_ang, c->T, n, c->delta, c->kb);

@@ -154,6 +154,22 @@ def planar_receivers(side: int, pitch: float, z: float) -> np.ndarray:
     return np.stack([X.ravel(), Y.ravel(), np.full(side * side, z)], axis=1)
 
 
+def polarised_hemisphere(n_polar: int = 9, n_azimuth: int = 9) -> np.ndarray:
+    """[n_polar x n_azimuth, 6] unit propagation directions over the upper
+    hemisphere (polar angles (i + 0.5) 90 / n_polar degrees from +z, azimuths
+    360 j / n_azimuth) with the polar unit vector theta^ as polarisation
+    (orthogonal to the direction)."""
+    out = []
+    for i in range(n_polar):
+        th = np.radians((i + 0.5) * 90.0 / n_polar)
+        for j in range(n_azimuth):
+            ph = 2.0 * np.pi * j / n_azimuth
+            d = [np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)]
+            p = [np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)]
+            out.append(d + p)
+    return np.array(out)
+
+
 def circle_sources(T: int, radius: float, offset: float = 0.0) -> np.ndarray:
     """[T, 2] source positions uniformly spaced on a circle, starting at angle ``offset``."""
     phi = offset + 2.0 * np.pi * np.arange(T) / T
@@ -213,6 +229,16 @@ CONFIGS = {
     "c6": dict(dim=2, n=128, delta=1.5 / 128, T=8, M=360, rx_radius=7.6, tx_radius=7.2, tx_kind="point",
                rx_min_deg=60.0, shapes=3, contrast=(0.0, 1.0), imag=0.0, snr_db=40.0, outer=100, tau=1e-3,
                tv_iters=20, alpha=0.96, seed=1714),
+    # 3D vectorial (appendix): the sizes of the 3D experimental set-up of Sec.
+    # IV at 4 GHz (lambda = 75 mm): a 150 mm cube on 32^3 voxels (delta =
+    # lambda / 16), 81 polarised plane waves over the upper hemisphere (9
+    # polar x 9 azimuth, theta-polarised), 36 receivers on a circle of 20
+    # lambda in the azimuth plane measuring E_z, each transmitter recording the
+    # receivers more than 50 degrees from its azimuth; 2 seeded spheres with
+    # contrast up to 1.5 stand in for the measured objects.
+    "c7": dict(dim=3, vectorial=True, n=32, delta=1.0 / 16, T=81, M=36, rx_radius=20.0, rx_min_deg=50.0,
+               shapes=2, contrast=(0.5, 1.5), imag=0.0, snr_db=40.0, outer=50, tau=1e-3, tv_iters=20,
+               alpha=0.96, seed=1715),
 }
 
 
@@ -221,6 +247,13 @@ def make_inputs(name: str, T: int | None = None):
     cfg = dict(CONFIGS[name])
     if T is not None:
         cfg["T"] = T
+    if cfg.get("vectorial"):
+        f = sphere_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
+        tx = polarised_hemisphere()[: cfg["T"]]
+        rx3 = circle_receivers(cfg["M"], cfg["rx_radius"])
+        rx = np.concatenate([rx3, np.zeros((cfg["M"], 1))], axis=1)
+        cfg["rx_mask"] = angular_mask(tx[:, :2], rx3, cfg["rx_min_deg"])
+        return cfg, f, tx, rx
     if cfg["dim"] == 3:
         f = sphere_phantom(cfg["n"], cfg["shapes"], cfg["contrast"], cfg["seed"], cfg["imag"])
         tx = hemisphere_directions()[: cfg["T"]]
