@@ -12,7 +12,9 @@ counts LS field solves (forward + adjoint) per second.
 
 ``--config c3`` runs the 3D workload instead: 64^3 voxels at lambda/6 (FFT
 128^3), 48 plane waves over the upper hemisphere, 1024 receivers on a plane,
-5 seeded random spheres with contrast up to 0.3.  ``--config c6`` runs a
+5 seeded random spheres with contrast up to 0.3.  ``--config c7`` runs the 3D
+vectorial model of the appendix (32^3 voxels, 81 polarised plane waves, 36
+receivers measuring E_z).  ``--config c6`` runs a
 Fresnel-style 2D set-up: 8 line sources, 360 receivers of which each source
 records the 240 farther than 60 degrees from it.
 
@@ -134,6 +136,15 @@ def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
     """Cold-start FP64 oracle forward solves of the given transmitters; returns (solves, seconds, note, fields)."""
     from oracle import model, solve
     n, dim = cfg["n"], cfg["dim"]
+    if cfg.get("vectorial"):
+        from oracle import vector
+        tx = np.asarray(angles)[list(txs)]
+        prob = vector.VectorProblem(n, cfg["delta"], tx[:, :3], tx[:, 3:], rx)
+        t0 = time.perf_counter()
+        xs = vector.solve_fields(prob, f_point, prob.u_in, tol)
+        sec = time.perf_counter() - t0
+        return len(txs), sec, (f"{len(txs)} cold-start vectorial forward solves (transmitters {txs[0]}-{txs[-1]}) "
+                               f"to residual {tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"), list(xs)
     shape = (n,) * dim
     prob = model.Problem(n, cfg["delta"], np.asarray(angles)[list(txs)], rx, dim=dim,
                          tx_kind=cfg.get("tx_kind", "plane"))
@@ -146,21 +157,48 @@ def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
                            f"{tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"), [x.reshape(shape) for x in xs]
 
 
-def _cufft_matvec_ms(ctx, f_dev, x_dev, dim, reps=20):
+def _graddiv_torch(C, delta):
+    """Comparison only: the appendix's finite-difference grad-div of [B, 3, n, n, n] fields (zero outside)."""
+    import torch
+    P = torch.nn.functional.pad(C, (1, 1, 1, 1, 1, 1))
+    n = C.shape[-1]
+    ax = {0: -1, 1: -2, 2: -3}
+
+    def sh(a, offs):
+        sl = [slice(1, n + 1)] * 3
+        for comp, o in offs.items():
+            sl[3 + ax[comp]] = slice(1 + o, n + 1 + o)
+        return a[(Ellipsis,) + tuple(sl)]
+
+    out = []
+    for c in range(3):
+        acc = (sh(P[:, c], {c: 1}) - 2 * sh(P[:, c], {}) + sh(P[:, c], {c: -1})) / delta ** 2
+        for j in range(3):
+            if j != c:
+                acc = acc + (sh(P[:, j], {c: -1, j: -1}) - sh(P[:, j], {c: -1, j: 1}) - sh(P[:, j], {c: 1, j: -1})
+                             + sh(P[:, j], {c: 1, j: 1})) / (4 * delta ** 2)
+        out.append(acc)
+    return torch.stack(out, 1)
+
+
+def _cufft_matvec_ms(ctx, f_dev, x_dev, dim, reps=20, vectorial=False, delta=1.0, k=2 * np.pi):
     """Comparison only (never on the product path): the same batched A x with torch.fft (cuFFT):
-    zero-pad f x to P^d, FFT, times the library's own spectrum, inverse FFT, crop, subtract."""
+    zero-pad f x to P^d, FFT, times the library's own spectrum, inverse FFT, crop, subtract
+    (vectorial: per component, then the grad-div stencil)."""
     import torch
     P, n = ctx.P, ctx.n
     gh = torch.empty((P,) * dim, dtype=torch.complex64, device=x_dev.device)
     ctx.green_spectrum(gh)
     axes = tuple(range(-dim, 0))
-    crop = (slice(None),) + (slice(0, n),) * dim
-    pad = torch.zeros((x_dev.shape[0],) + (P,) * dim, dtype=torch.complex64, device=x_dev.device)
+    crop = (Ellipsis,) + (slice(0, n),) * dim
+    pad = torch.zeros(x_dev.shape[:-dim] + (P,) * dim, dtype=torch.complex64, device=x_dev.device)
 
     def once():
         pad[crop] = f_dev * x_dev
-        y = torch.fft.ifftn(torch.fft.fftn(pad, dim=axes) * gh, dim=axes)
-        return x_dev - y[crop]
+        y = torch.fft.ifftn(torch.fft.fftn(pad, dim=axes) * gh, dim=axes)[crop]
+        if vectorial:
+            return x_dev - y - _graddiv_torch(y, delta) / k ** 2
+        return x_dev - y
 
     for _ in range(3):
         once()
@@ -176,6 +214,10 @@ def _cufft_matvec_ms(ctx, f_dev, x_dev, dim, reps=20):
 
 def _workload(name, cfg):
     T, M = cfg["T"], cfg["M"]
+    if cfg.get("vectorial"):
+        return (f"{name}: 3D vectorial (appendix), 32^3 voxels at lambda/16, FFT 64^3 per component, {T} polarised "
+                f"plane waves over the upper hemisphere, {M} Rx measuring E_z on a circle of {cfg['rx_radius']} lambda, "
+                f"receivers within {cfg['rx_min_deg']:.0f} deg masked off, 2 spheres contrast<=1.5, 40 dB")
     if cfg.get("tx_kind") == "point":
         return (f"{name}: Fresnel-style 2D, 128x128 over 1.5 lambda, FFT 256x256, {T} line sources at "
                 f"{cfg['tx_radius']} lambda, {M} Rx at {cfg['rx_radius']} lambda, receivers within "
@@ -262,7 +304,9 @@ def main():
     cfg, f_true, angles, rx = synth.make_inputs(args.config)
     n, T, M, dim = cfg["n"], cfg["T"], cfg["M"], cfg["dim"]
     complex_f = cfg["imag"] != 0.0
-    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim, tx_kind=cfg.get("tx_kind", 0))
+    vec = bool(cfg.get("vectorial"))
+    ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim, tx_kind=cfg.get("tx_kind", 0),
+                      vectorial=vec)
     if "rx_mask" in cfg:
         ctx.set_rx_mask(cfg["rx_mask"])
     cols_nt = ctx.autotune(reps=10)  # pick the column-FFT CTA shape by measurement
@@ -275,9 +319,9 @@ def main():
     noise = torch.from_numpy(synth.complex_noise(cfg["seed"] + 100, (T, M)).astype(np.complex64)).to(dev)
     sigma = float(torch.linalg.vector_norm(y_dev)) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(T * M)
     y_dev += sigma * noise
-    H_dev = torch.empty((M, ctx.N), dtype=torch.complex64, device=dev)
+    H_dev = torch.empty((M, ctx.Nf), dtype=torch.complex64, device=dev)
     ctx.sensing_matrix(H_dev)
-    u_in = torch.empty((T, ctx.N), dtype=torch.complex64, device=dev)
+    u_in = torch.empty((T, ctx.Nf), dtype=torch.complex64, device=dev)
     ctx.incident(u_in)
     # L_Born <= T max|u_in|^2 ||H||_F^2 (max |u_in| = 1 for plane waves)
     gamma = 1.0 / (T * float(u_in.abs().max()) ** 2 * float(torch.linalg.vector_norm(H_dev)) ** 2)
@@ -313,7 +357,7 @@ def main():
     # Working sets smaller than twice L2 (129 MB) are timed step by step with an
     # L2 flush (a 512 MB write) between the steps, outside the timed windows;
     # larger ones stream through L2 by themselves and are timed back to back.
-    working = 12 * T * ctx.N * 8 + M * ctx.N * 8
+    working = 12 * T * ctx.Nf * 8 + M * ctx.Nf * 8
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev) if working < 2 * (129 << 20) else None
     if flush is None:
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -381,16 +425,18 @@ def main():
     mv_ms = ctx.time_matvec(s0, adjoint=False, reps=20)
     N = ctx.N
     Pd = ctx.P ** dim
-    alg_bytes = T * 16 * N + 8 * N                       # read x, write y per transmitter, f once
-    alg_flops = T * 2 * 5 * Pd * np.log2(Pd)             # forward + inverse P^d FFT per transmitter (unpruned)
+    ncomp = 3 if vec else 1
+    alg_bytes = T * 16 * ctx.Nf + 8 * N                  # read x, write y per transmitter, f once
+    alg_flops = ncomp * T * 2 * 5 * Pd * np.log2(Pd)     # forward + inverse P^d FFT per field component (unpruned)
     achieved_tf = alg_flops / (mv_ms * 1e-3) / 1e12
     achieved_gbs = alg_bytes / (mv_ms * 1e-3) / 1e9
     hbm_peak, peak_kind = _peaks()
     fp32_peak = FP32_PEAK_TFLOPS
     traffic = _traffic_summary(args.config)
-    u_in = torch.empty((T,) + (n,) * dim, dtype=torch.complex64, device=dev)
+    fshape = (T, 3) + (n,) * dim if vec else (T,) + (n,) * dim
+    u_in = torch.empty(fshape, dtype=torch.complex64, device=dev)
     ctx.incident(u_in)
-    cufft_ms = _cufft_matvec_ms(ctx, s0, u_in, dim)
+    cufft_ms = _cufft_matvec_ms(ctx, s0, u_in, dim, vectorial=vec, delta=cfg["delta"], k=2 * np.pi)
     del u_in
 
     cpu = None
@@ -405,7 +451,7 @@ def main():
         cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note}
         # error of the converged field (GPU, residual tol) against a tight FP64 oracle solve of transmitter 0
         _, _, _, ref = _oracle_sample_solves(cfg, s0n, angles, rx, [0], 1e-9)
-        u_dev = torch.empty((T,) + (n,) * dim, dtype=torch.complex64, device=dev)
+        u_dev = torch.empty((T, 3) + (n,) * dim if vec else (T,) + (n,) * dim, dtype=torch.complex64, device=dev)
         ctx.forward(s0, u_out=u_dev, tol=args.tol, max_iter=args.max_iter, check=False)
         u0 = u_dev[0].cpu().numpy().astype(np.complex128)
         field_err = {"rel_l2": float(np.linalg.norm(u0 - ref[0]) / np.linalg.norm(ref[0])),
@@ -439,7 +485,8 @@ def main():
                          "frac": achieved_tf / fp32_peak, "traffic": traffic,
                          "kernel": "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols + conv_rows_inv)"
                                    if dim == 2 else "batched FFT matvec A x over all T (conv_rows_fwd + conv_cols "
-                                   "y-forward + conv_cols z-spectrum + conv_cols y-inverse + conv_rows_inv)",
+                                   "y-forward + conv_cols z-spectrum + conv_cols y-inverse + conv_rows_inv"
+                                   + (" per field component, + the grad-div stencil)" if vec else ")"),
                          "ms_per_launch": mv_ms, "alg_flops_per_launch": alg_flops,
                          "alg_bytes_per_launch": alg_bytes,
                          "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 x 2.07 GHz",

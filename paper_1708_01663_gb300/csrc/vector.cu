@@ -28,28 +28,29 @@
 
 namespace cisor {
 
-// (D F)^(c) at voxel (ix, iy, iz) of the 3-component field F (component stride N)
-__device__ __forceinline__ float2 graddiv_at(const float2* __restrict__ F, long long N, int n, int ix, int iy, int iz,
-                                            long long v, int c, float inv_d2) {
+// (D F)^(C) at voxel v = (ix, iy, iz) of the 3-component field F (component stride N)
+template <int C>
+__device__ __forceinline__ float2 graddiv_at(const float2* __restrict__ F, int N, int n, int ix, int iy, int iz, int v,
+                                            float inv_d2) {
   const int coord[3] = {ix, iy, iz};
-  const long long stride[3] = {1, n, (long long)n * n};
-  const float2* Fc = F + c * N;
+  const int stride[3] = {1, n, n * n};
+  const float2* Fc = F + C * N;
   float2 acc = c_scale(Fc[v], -2.f);
-  if (coord[c] > 0) acc = c_add(acc, Fc[v - stride[c]]);
-  if (coord[c] < n - 1) acc = c_add(acc, Fc[v + stride[c]]);
+  if (coord[C] > 0) acc = c_add(acc, Fc[v - stride[C]]);
+  if (coord[C] < n - 1) acc = c_add(acc, Fc[v + stride[C]]);
   acc = c_scale(acc, inv_d2);
   float2 mix = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    if (j == c) continue;
+    if (j == C) continue;
     const float2* Fj = F + j * N;
 #pragma unroll
     for (int sc = -1; sc <= 1; sc += 2)
 #pragma unroll
       for (int sj = -1; sj <= 1; sj += 2) {
-        const int qc = coord[c] + sc, qj = coord[j] + sj;
+        const int qc = coord[C] + sc, qj = coord[j] + sj;
         if (qc < 0 || qc >= n || qj < 0 || qj >= n) continue;
-        const float2 val = Fj[v + sc * stride[c] + sj * stride[j]];
+        const float2 val = Fj[v + sc * stride[C] + sj * stride[j]];
         mix = (sc * sj > 0) ? c_add(mix, val) : c_sub(mix, val);
       }
   }
@@ -71,32 +72,31 @@ struct VecEpiArgs {
   float inv_k2, inv_d2;
 };
 
-// One CTA: RB x rows (RB n voxels) of component blockIdx.y of transmitter blockIdx.z.
-__global__ void __launch_bounds__(256) vec_stencil_kernel(const VecEpiArgs a) {
-  const int rb = blockIdx.x, c = blockIdx.y, t = blockIdx.z;
-  if (a.active && !a.active[t]) return;
-  const long long N = a.N;
-  const int n = a.n;
+// RB x rows (RB n voxels) of component C of transmitter blockIdx.z (N < 2^31: n <= 64).
+template <int C>
+__device__ __forceinline__ void vec_stencil_body(const VecEpiArgs& a) {
+  const int rb = blockIdx.x, t = blockIdx.z;
+  const int N = (int)a.N, n = a.n;
   const long long base = (long long)t * 3 * N;
   const float2* F = a.C + base;
-  const long long v0 = (long long)rb * a.RB * n;
-  const long long v1 = min(N, v0 + (long long)a.RB * n);
+  const int v0 = rb * a.RB * n;
+  const int v1 = min(N, v0 + a.RB * n);
   const bool any_dot = a.epi >= 0 && (a.dot_a[0] | a.dot_a[1] | a.dot_a[2]) != 0;
   const bool need_aux = a.epi == EPI_RESID || a.dot_a[0] == OP_AUX || a.dot_b[0] == OP_AUX ||
                         a.dot_a[1] == OP_AUX || a.dot_b[1] == OP_AUX || a.dot_a[2] == OP_AUX || a.dot_b[2] == OP_AUX;
   float2 acc[DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) acc[s] = make_float2(0.f, 0.f);
-  for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-    const int ix = (int)(v % n), iy = (int)((v / n) % n), iz = (int)(v / ((long long)n * n));
-    const float2 dc = graddiv_at(F, N, n, ix, iy, iz, v, c, a.inv_d2);
-    const long long idx = base + c * N + v;
+  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int row = v / n, ix = v - row * n, iz = row / n, iy = row - iz * n;
+    const float2 dc = graddiv_at<C>(F, N, n, ix, iy, iz, v, a.inv_d2);
+    const long long idx = base + (long long)C * N + v;
     if (a.epi < 0) {  // pre-pass of the adjoint: w = x + D x / k^2
-      a.out[idx] = c_add(F[c * N + v], c_scale(dc, a.inv_k2));
+      a.out[idx] = c_add(F[C * N + v], c_scale(dc, a.inv_k2));
       continue;
     }
     const float2 xv = a.x[idx];
-    float2 y = c_sub(c_sub(xv, F[c * N + v]), c_scale(dc, a.inv_k2));
+    float2 y = c_sub(c_sub(xv, F[C * N + v]), c_scale(dc, a.inv_k2));
     const float2 av = need_aux ? a.aux[idx] : make_float2(0.f, 0.f);
     if (a.epi == EPI_RESID) y = c_sub(av, y);
     a.out[idx] = y;
@@ -108,7 +108,17 @@ __global__ void __launch_bounds__(256) vec_stencil_kernel(const VecEpiArgs a) {
     }
   }
   if (any_dot)
-    block_dots<256>(acc, reinterpret_cast<float2*>(a.part) + (((size_t)t * 3 + c) * a.nblk + rb) * DOT_SLOTS);
+    block_dots<256>(acc, reinterpret_cast<float2*>(a.part) + (((size_t)t * 3 + C) * a.nblk + rb) * DOT_SLOTS);
+}
+
+// One CTA: RB x rows of component blockIdx.y of transmitter blockIdx.z.
+__global__ void __launch_bounds__(256) vec_stencil_kernel(const VecEpiArgs a) {
+  if (a.active && !a.active[blockIdx.z]) return;
+  switch (blockIdx.y) {
+    case 0: vec_stencil_body<0>(a); break;
+    case 1: vec_stencil_body<1>(a); break;
+    default: vec_stencil_body<2>(a); break;
+  }
 }
 
 static VecEpiArgs stencil_args(cisor_ctx* c) {

@@ -32,7 +32,7 @@ def main():
     build.build()
     cfg, f, angles, rx = synth.make_inputs(args.config, T=args.T)
     ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles, rx, complex_f=cfg["imag"] != 0.0, dim=cfg["dim"],
-                      tx_kind=cfg.get("tx_kind", 0))
+                      tx_kind=cfg.get("tx_kind", 0), vectorial=bool(cfg.get("vectorial")))
     fd = torch.from_numpy(np.ascontiguousarray(0.9 * f, dtype=np.complex64)).cuda()
     if args.cols_cta:
         ctx.set_cols_cta(args.cols_cta)
