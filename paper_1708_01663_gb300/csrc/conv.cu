@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   const bool rowok = iy < geo.nrows;
   const long long N = (long long)geo.nrows * n;
   for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 256) tw[i] = tw_g[i];
+  __syncthreads();  // the twiddle table is shared by the rows, whose exchanges sync per row
   float2 alpha = make_float2(0.f, 0.f), beta = alpha, omega = alpha;
   if (PRO != PRO_COPY) {
     const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)txs * SC_STRIDE;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
       }
       v[q * R0 + r] = val;
     }
-  reg_fft<P, false, false>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw);
+  reg_fft<P, false, false>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw, RowSync<P>{row});
   if (!rowok) return;
   constexpr int RL = PL::template last<false>();
   float2* dst = R + r_row<P>(geo, tx, iy);
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   const bool rowok = iy < geo.nrows;
   const long long N = (long long)geo.nrows * n;
   for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 256) tw[i] = tw_g[TW_STRIDE + i];
+  __syncthreads();  // the twiddle table is shared by the rows, whose exchanges sync per row
   constexpr int R0 = PL::template first<true>();
   const float2* srow = R + r_row<P>(geo, tx, rowok ? iy : 0);
   float2 v[8];
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
       pre_src[q * RL + r] = (ok && EPI != EPI_CONV_ADD) ? op.esrc[idx] : make_float2(0.f, 0.f);
       pre_aux[q * RL + r] = (ok && need_aux) ? op.aux[idx] : make_float2(0.f, 0.f);
     }
-  reg_fft<P, true, true>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw);
+  reg_fft<P, true, true>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw, RowSync<P>{row});
   float2 acc[DOT_SLOTS];
 #pragma unroll
   for (int s = 0; s < DOT_SLOTS; ++s) acc[s] = make_float2(0.f, 0.f);

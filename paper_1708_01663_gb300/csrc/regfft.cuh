@@ -117,11 +117,30 @@ __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __re
   }
 }
 
+// Barriers around an exchange.  CtaSync: the whole CTA (transforms that span
+// all warps, e.g. the column kernels).  RowSync: only the P/8 threads of one
+// row transform, whose exchange region no other row touches -- a named
+// barrier (id 1 + row) when the transform spans whole warps, the warp
+// otherwise -- so the rows of a CTA do not wait for one another.
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int P> struct RowSync {
+  int row;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (P / 8 >= 32)
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + row), "r"(P / 8) : "memory");
+    else
+      __syncwarp();
+  }
+};
+
 // outputs of a stage (radix RO, size NS) to shared memory, then the inputs of the next stage (radix RI)
-template <int P, int RO, int NS, int RI, class LAY>
-__device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY& lay, int t) {
+template <int P, int RO, int NS, int RI, class LAY, class SYNC = CtaSync>
+__device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY& lay, int t,
+                                          const SYNC& sync = SYNC()) {
   constexpr int NTF = P / 8;
-  __syncthreads();
+  sync();
 #pragma unroll
   for (int q = 0; q < 8 / RO; ++q) {
     const int j = t + q * NTF;
@@ -130,7 +149,7 @@ __device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY
 #pragma unroll
     for (int r = 0; r < RO; ++r) buf[lay(base + r * NS)] = v[q * RO + r];
   }
-  __syncthreads();
+  sync();
 #pragma unroll
   for (int q = 0; q < 8 / RI; ++q) {
     const int j = t + q * NTF;
@@ -142,15 +161,15 @@ __device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY
 // Transform the registers v in place (see the file comment for the element
 // mapping); tws is this plan's stage twiddle table (TwTable<P, REV>); lay0 and
 // lay1 are the shared-memory layouts of the first and second exchange.
-template <int P, bool INV, bool REV, class LAY0, class LAY1>
+template <int P, bool INV, bool REV, class LAY0, class LAY1, class SYNC = CtaSync>
 __device__ __forceinline__ void reg_fft(float2 (&v)[8], float2* buf, const LAY0& lay0, const LAY1& lay1, int t,
-                                        const float2* __restrict__ tws) {
+                                        const float2* __restrict__ tws, const SYNC& sync = SYNC()) {
   typedef TwTable<P, REV> TT;
   rstage<P, TT::R0, 1, INV>(v, t, tws);
-  rexchange<P, TT::R0, 1, TT::R1>(v, buf, lay0, t);
+  rexchange<P, TT::R0, 1, TT::R1>(v, buf, lay0, t, sync);
   rstage<P, TT::R1, TT::R0, INV>(v, t, tws + TT::OFF1);
   if constexpr (RPlan<P>::NSTAGE == 3) {
-    rexchange<P, TT::R1, TT::R0, TT::R2>(v, buf, lay1, t);
+    rexchange<P, TT::R1, TT::R0, TT::R2>(v, buf, lay1, t, sync);
     rstage<P, TT::R2, TT::R0 * TT::R1, INV>(v, t, tws + TT::OFF2);
   }
 }
