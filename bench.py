@@ -276,7 +276,8 @@ def _traffic_summary(config):
         for line in text.splitlines():
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
+                v = v.strip()
+                vals[k.strip()] = v.split("`")[1] if v.startswith("`") and v.count("`") >= 2 else v
         if vals.get("conv_sources_sha256_16") != conv_sources_hash():
             return None
         return float(vals["dram_bytes_per_pass"])

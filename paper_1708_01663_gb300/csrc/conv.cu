@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   const bool rowok = iy < geo.nrows;
   const long long N = (long long)geo.nrows * n;
   for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += 256) tw[i] = tw_g[i];
-  __syncthreads();  // the twiddle table is shared by the rows, whose exchanges sync per row
+  if (P / 8 < 32) __syncthreads();  // the twiddle table is shared by rows that sync per warp
   float2 alpha = make_float2(0.f, 0.f), beta = alpha, omega = alpha;
   if (PRO != PRO_COPY) {
     const double2* sc = reinterpret_cast<const double2*>(op.scal) + (size_t)txs * SC_STRIDE;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   const bool rowok = iy < geo.nrows;
   const long long N = (long long)geo.nrows * n;
   for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 256) tw[i] = tw_g[TW_STRIDE + i];
-  __syncthreads();  // the twiddle table is shared by the rows, whose exchanges sync per row
+  if (P / 8 < 32) __syncthreads();  // the twiddle table is shared by rows that sync per warp
   constexpr int R0 = PL::template first<true>();
   const float2* srow = R + r_row<P>(geo, tx, rowok ? iy : 0);
   float2 v[8];

@@ -118,10 +118,12 @@ __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __re
 }
 
 // Barriers around an exchange.  CtaSync: the whole CTA (transforms that span
-// all warps, e.g. the column kernels).  RowSync: only the P/8 threads of one
-// row transform, whose exchange region no other row touches -- a named
-// barrier (id 1 + row) when the transform spans whole warps, the warp
-// otherwise -- so the rows of a CTA do not wait for one another.
+// all warps, e.g. the column kernels).  RowSync: row transforms, whose
+// exchange regions no other row touches; when a row fits in one warp (P <= 128)
+// the warp's own barrier suffices and the rows of a CTA do not wait for one
+// another.  Wider rows keep the CTA barrier: per-row named barriers measured
+// slower there (the P = 512 row kernel fell from 88 % to 42 % achieved
+// occupancy).
 struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
@@ -129,7 +131,7 @@ template <int P> struct RowSync {
   int row;
   __device__ __forceinline__ void operator()() const {
     if constexpr (P / 8 >= 32)
-      asm volatile("bar.sync %0, %1;" ::"r"(1 + row), "r"(P / 8) : "memory");
+      __syncthreads();
     else
       __syncwarp();
   }
