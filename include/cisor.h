@@ -10,7 +10,10 @@
  *
  * Conventions for every entry point:
  *  - complex arrays are interleaved complex64 (float re, float im), row-major
- *    with the x index fastest; fields are transmitter-major [T, n, n];
+ *    with the x index fastest; N = n^dim pixels; fields are transmitter-major
+ *    [T, N] ([T, n, n] in 2D, [T, n, n, n] in 3D).  For a vectorial geometry
+ *    every field written [T, N] below is [T, 3, N] (E^(1), E^(2), E^(3)) and H
+ *    is [M, 3N]; f, gradients and prox arrays stay [N];
  *  - array arguments may be device or host pointers: inputs are copied into
  *    the context's device buffers and results out of them with
  *    cudaMemcpyDefault (unified addressing); a call that writes host memory
