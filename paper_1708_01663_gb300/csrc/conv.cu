@@ -60,7 +60,8 @@ struct RowGeo {
 };
 template <int P>
 __device__ __forceinline__ long long r_row(const RowGeo& g, int tx, int q) {
-  return tx * g.tstride + (long long)(q / g.n) * g.slab + (long long)(q % g.n) * P;
+  const int z = q < g.n ? 0 : q / g.n;  // 2D rows never divide
+  return tx * g.tstride + (long long)z * g.slab + (long long)(q - z * g.n) * P;
 }
 
 template <int P, int PRO>
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
     for (int r = 0; r < R0; ++r) {
       const int ix = PL::elem(lt, q, r, R0);
       float2 val = make_float2(0.f, 0.f);
-      if (rowok && ix < n) {
+      if (PL::lower(q, r, R0) && rowok && ix < n) {  // n <= P/2: the upper half is padding
         const long long pix = (long long)iy * n + ix;
         const long long idx = tx * N + pix;
         if (PRO == PRO_COPY) {
@@ -117,7 +118,8 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
       }
       v[q * R0 + r] = val;
     }
-  reg_fft<P, false, false>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw, RowSync<P>{row});
+  reg_fft<P, false, false, true>(v, buf, RowLayA<P>{row * C::PP}, RowLayB<P>{row * C::PP}, lt, tw,
+                                 RowSync<P>{row});
   if (!rowok) return;
   constexpr int RL = PL::template last<false>();
   float2* dst = R + r_row<P>(geo, tx, iy);
@@ -181,9 +183,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
 #pragma unroll
       for (int r = 0; r < R0; ++r) {
         const int i = PL::elem(lt, q, r, R0);
-        v[q * R0 + r] = (i < n) ? base[i * es] : make_float2(0.f, 0.f);
+        v[q * R0 + r] = (PL::lower(q, r, R0) && i < n) ? base[i * es] : make_float2(0.f, 0.f);
       }
-    reg_fft<P, false, false>(v, buf, lay, lay, lt, tw);
+    reg_fft<P, false, false, true>(v, buf, lay, lay, lt, tw);
   }
   constexpr int RL = PL::template last<false>();
   if (MODE == COL_FWD) {
@@ -212,11 +214,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
       const int i = PL::elem(lt, q, r, RI);
-      if (i < n) base[i * es] = v[q * RI + r];
+      if (PL::lower(q, r, RI) && i < n) base[i * es] = v[q * RI + r];
     }
 }
 
-template <int P, int EPI>
+// Inner-product sets of the inverse-row epilogue.  The solver's three are
+// compiled with fixed operands; DOTS_ANY reads the operand codes of ConvOp.
+//   DOTS_RV : slot 0 <aux, y>               (<rhat, v>, v = A p)
+//   DOTS_TS : slot 1 <y, src>, slot 2 <y, y> (<t, s>, <t, t>, t = A s)
+//   DOTS_RES: slot 0 <aux, aux>, slot 2 <y, y> (<b, b>, <r, r>, r = b - A x)
+enum { DOTS_NONE = 0, DOTS_RV = 1, DOTS_TS = 2, DOTS_RES = 3, DOTS_ANY = 4 };
+
+static int dots_kind(const ConvOp& op) {
+  auto is = [&](int a0, int b0, int a1, int b1, int a2, int b2) {
+    return op.dot_a[0] == a0 && op.dot_b[0] == b0 && op.dot_a[1] == a1 && op.dot_b[1] == b1 &&
+           op.dot_a[2] == a2 && op.dot_b[2] == b2;
+  };
+  if (is(0, 0, 0, 0, 0, 0)) return DOTS_NONE;
+  if (is(OP_AUX, OP_Y, 0, 0, 0, 0)) return DOTS_RV;
+  if (is(0, 0, OP_Y, OP_SRC, OP_Y, OP_Y)) return DOTS_TS;
+  if (is(OP_AUX, OP_AUX, 0, 0, OP_Y, OP_Y)) return DOTS_RES;
+  return DOTS_ANY;
+}
+
+template <int DK> struct DotSlots {
+  static constexpr int MASK = DK == DOTS_NONE ? 0 : DK == DOTS_RV ? 1 : DK == DOTS_TS ? 6 : DK == DOTS_RES ? 5 : 7;
+};
+
+template <int P, int EPI, int DK>
 __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const float2* __restrict__ tw_g,
                                                      const float2* __restrict__ R, const RowGeo geo, int nblk) {
   typedef ConvCfg<P> C;
@@ -240,16 +265,18 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
 #pragma unroll
     for (int r = 0; r < R0; ++r) v[q * R0 + r] = rowok ? srow[PL::elem(lt, q, r, R0)] : make_float2(0.f, 0.f);
   const bool postf = op.mul_f && op.adjoint;
-  const bool any_dot = (op.dot_a[0] | op.dot_a[1] | op.dot_a[2]) != 0;
-  const bool aux0 = EPI == EPI_MATVEC && (op.dot_a[0] == OP_AUX || op.dot_b[0] == OP_AUX);
-  const bool need_aux = EPI == EPI_RESID || aux0 || (EPI == EPI_CONV_ADD && op.aux);
+  bool need_aux = EPI == EPI_RESID || (EPI == EPI_CONV_ADD && op.aux) || DK == DOTS_RV || DK == DOTS_RES;
+  if (DK == DOTS_ANY)
+    for (int s = 0; s < DOT_SLOTS; ++s) need_aux |= op.dot_a[s] == OP_AUX || op.dot_b[s] == OP_AUX;
   constexpr int RL = PL::template last<true>();
-  // epilogue operands are loaded before the transform so their latency overlaps it
+  // epilogue operands are loaded before the transform so their latency overlaps
+  // it; only outputs below P/2 can be kept (n <= P/2)
   float2 pre_src[8], pre_aux[8];
 #pragma unroll
   for (int q = 0; q < 8 / RL; ++q)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
+      if (!PL::lower(q, r, RL)) continue;
       const int ix = PL::elem(lt, q, r, RL);
       const bool ok = rowok && ix < n;
       const long long idx = tx * N + (long long)(rowok ? iy : 0) * n + (ix < n ? ix : 0);
@@ -265,6 +292,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
     for (int q = 0; q < 8 / RL; ++q)
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
+        if (!PL::lower(q, r, RL)) continue;
         const int ix = PL::elem(lt, q, r, RL);
         if (ix >= n) continue;
         const long long pix = (long long)iy * n + ix;
@@ -282,7 +310,15 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
         }
         op.out[idx] = y;
         if (op.out2) op.out2[idx] = y;
-        if (any_dot) {
+        if constexpr (DK == DOTS_RV) {
+          acc[0] = c_add(acc[0], c_cjmul(aux, y));
+        } else if constexpr (DK == DOTS_TS) {
+          acc[1] = c_add(acc[1], c_cjmul(y, src));
+          acc[2].x = fmaf(y.x, y.x, fmaf(y.y, y.y, acc[2].x));
+        } else if constexpr (DK == DOTS_RES) {
+          acc[0].x = fmaf(aux.x, aux.x, fmaf(aux.y, aux.y, acc[0].x));
+          acc[2].x = fmaf(y.x, y.x, fmaf(y.y, y.y, acc[2].x));
+        } else if constexpr (DK == DOTS_ANY) {
 #pragma unroll
           for (int s = 0; s < DOT_SLOTS; ++s) {
             if (op.dot_a[s]) {
@@ -293,7 +329,8 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
         }
       }
   }
-  if (any_dot) block_dots<256>(acc, reinterpret_cast<float2*>(op.part) + ((size_t)tx * nblk + blockIdx.x) * DOT_SLOTS);
+  if constexpr (DK != DOTS_NONE)
+    block_dots<256, DotSlots<DK>::MASK>(acc, reinterpret_cast<float2*>(op.part) + ((size_t)tx * nblk + blockIdx.x) * DOT_SLOTS);
 }
 
 template <int P, int MODE, bool ADJ, int NT>
@@ -349,11 +386,25 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
     cols_pass<P, COL_G>(c, op, 1, P, 0);
   }
   CISOR_CUDA(cudaGetLastError());
+  const int dk = dots_kind(op);
+#define CISOR_ROWS_INV(E, D) conv_rows_inv<P, E, D><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg, c->nblk)
   switch (op.epilogue) {
-    case EPI_MATVEC: conv_rows_inv<P, EPI_MATVEC><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg, c->nblk); break;
-    case EPI_RESID: conv_rows_inv<P, EPI_RESID><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg, c->nblk); break;
-    default: conv_rows_inv<P, EPI_CONV_ADD><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg, c->nblk); break;
+    case EPI_MATVEC:
+      if (dk == DOTS_NONE) CISOR_ROWS_INV(EPI_MATVEC, DOTS_NONE);
+      else if (dk == DOTS_RV) CISOR_ROWS_INV(EPI_MATVEC, DOTS_RV);
+      else if (dk == DOTS_TS) CISOR_ROWS_INV(EPI_MATVEC, DOTS_TS);
+      else CISOR_ROWS_INV(EPI_MATVEC, DOTS_ANY);
+      break;
+    case EPI_RESID:
+      if (dk == DOTS_RES) CISOR_ROWS_INV(EPI_RESID, DOTS_RES);
+      else CISOR_ROWS_INV(EPI_RESID, DOTS_ANY);
+      break;
+    default:
+      if (dk == DOTS_NONE) CISOR_ROWS_INV(EPI_CONV_ADD, DOTS_NONE);
+      else CISOR_ROWS_INV(EPI_CONV_ADD, DOTS_ANY);
+      break;
   }
+#undef CISOR_ROWS_INV
   CISOR_CUDA(cudaGetLastError());
   c->launches += conv_kernels_per_pass(c->dim);
   return CISOR_OK;

@@ -9,8 +9,9 @@ __device__ __forceinline__ float2 pick(int code, float2 y, float2 s, float2 a) {
 }
 
 // Block-wide sum of three complex FP32 partials: warp shuffles, then the
-// per-warp sums pairwise in shared memory (all FP32), written to part.
-template <int NT>
+// per-warp sums pairwise in shared memory (all FP32), written to part.  Only
+// the slots in MASK (bit s: slot s) are reduced; the others are written as 0.
+template <int NT, int MASK = 7>
 __device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], float2* out) {
   __shared__ float red[2 * DOT_SLOTS][NT / 32];
   float v[2 * DOT_SLOTS];
@@ -21,22 +22,28 @@ __device__ __forceinline__ void block_dots(const float2 acc[DOT_SLOTS], float2* 
   }
 #pragma unroll
   for (int k = 0; k < 2 * DOT_SLOTS; ++k) {
+    if (!((MASK >> (k / 2)) & 1)) continue;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 2 * DOT_SLOTS; ++k) red[k][wid] = v[k];
+    for (int k = 0; k < 2 * DOT_SLOTS; ++k)
+      if ((MASK >> (k / 2)) & 1) red[k][wid] = v[k];
   }
   __syncthreads();
   if (threadIdx.x < 2 * DOT_SLOTS) {
     float* r = red[threadIdx.x];
+    float sum = 0.f;
+    if ((MASK >> (threadIdx.x / 2)) & 1) {
 #pragma unroll
-    for (int w = NT / 64; w > 0; w >>= 1)
+      for (int w = NT / 64; w > 0; w >>= 1)
 #pragma unroll
-      for (int i = 0; i < w; ++i) r[i] += r[i + w];
-    reinterpret_cast<float*>(out)[threadIdx.x] = r[0];
+        for (int i = 0; i < w; ++i) r[i] += r[i + w];
+      sum = r[0];
+    }
+    reinterpret_cast<float*>(out)[threadIdx.x] = sum;
   }
 }
 

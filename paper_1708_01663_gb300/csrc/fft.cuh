@@ -75,6 +75,29 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
   v[7] = f_sub(e3, w3o);
 }
 
+// radix-8 DFT of inputs whose upper half v[4..7] is zero (the first stage of a
+// transform of a zero-padded sequence, padding >= half the length): each
+// radix-4 half sees two non-zero inputs, so its first butterfly layer is a
+// copy: DFT4(a, b, 0, 0) = (a + b, a + rot(b), a - b, a - rot(b)).
+template <bool INV, typename C> __device__ __forceinline__ void dft8_lo(C* v) {
+  typedef typename cx<C>::R R;
+  const C re1 = f_rot<INV>(v[2]), ro1 = f_rot<INV>(v[3]);
+  C e0 = f_add(v[0], v[2]), e1 = f_add(v[0], re1), e2 = f_sub(v[0], v[2]), e3 = f_sub(v[0], re1);
+  C o0 = f_add(v[1], v[3]), o1 = f_add(v[1], ro1), o2 = f_sub(v[1], v[3]), o3 = f_sub(v[1], ro1);
+  const R h = (R)0.70710678118654752440;
+  C w1o = INV ? cx<C>::make(h * (o1.x - o1.y), h * (o1.x + o1.y)) : cx<C>::make(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  C w2o = f_rot<INV>(o2);
+  C w3o = INV ? cx<C>::make(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : cx<C>::make(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = f_add(e0, o0);
+  v[4] = f_sub(e0, o0);
+  v[1] = f_add(e1, w1o);
+  v[5] = f_sub(e1, w1o);
+  v[2] = f_add(e2, w2o);
+  v[6] = f_sub(e2, w2o);
+  v[3] = f_add(e3, w3o);
+  v[7] = f_sub(e3, w3o);
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft_r(C* v) {
   if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);

@@ -33,6 +33,9 @@ template <int P> struct RPlan {
   template <bool REV> __host__ __device__ static constexpr int last() { return radix<REV>(NSTAGE - 1); }
   // element held in register q*R + r at the input (R = first radix) / output (R = last radix)
   __host__ __device__ static constexpr int elem(int t, int q, int r, int R) { return t + q * NTF + r * (P / R); }
+  // register (q, r) holds an element below P/2 for every t (t < NTF): its offset
+  // q NTF + r P/R is a multiple of NTF, so the test is exact
+  __host__ __device__ static constexpr bool lower(int q, int r, int R) { return q + r * (8 / R) < 4; }
 };
 
 // Shared-memory layouts, chosen so that the 16 threads of a half-warp (which
@@ -87,9 +90,11 @@ constexpr int TW_STRIDE = 512;  // floats2 reserved per plan table
 
 // One stage on the thread's registers.  Only w = tws[k] (the r = 1 row of
 // the stage table) is read from shared memory; w^2 .. w^7 are formed by
-// complex products (depth 3), trading shared-memory loads for FMAs.
-template <int P, int R, int NS, bool INV>
+// complex products (depth 3), trading shared-memory loads for FMAs.  LO: the
+// upper half of each radix-8 input group is zero (first stage only).
+template <int P, int R, int NS, bool INV, bool LO = false>
 __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __restrict__ tws) {
+  static_assert(!LO || (R == 8 && NS == 1), "pruned inputs only in a radix-8 first stage");
   constexpr int NTF = P / 8;
 #pragma unroll
   for (int q = 0; q < 8 / R; ++q) {
@@ -113,7 +118,10 @@ __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __re
 #pragma unroll
       for (int r = 1; r < R; ++r) v[q * R + r] = c_mul(v[q * R + r], w[r]);
     }
-    dft_r<R, INV>(v + q * R);
+    if constexpr (LO)
+      dft8_lo<INV>(v + q * R);
+    else
+      dft_r<R, INV>(v + q * R);
   }
 }
 
@@ -163,11 +171,16 @@ __device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY
 // Transform the registers v in place (see the file comment for the element
 // mapping); tws is this plan's stage twiddle table (TwTable<P, REV>); lay0 and
 // lay1 are the shared-memory layouts of the first and second exchange.
-template <int P, bool INV, bool REV, class LAY0, class LAY1, class SYNC = CtaSync>
+// LO_IN: the input is a sequence zero-padded to P from at most P/2 samples.
+// With a radix-8 first stage its registers v[4..7] hold elements >= P/2, so
+// they are zero; the caller need not set them.  A caller that wants only the
+// outputs below P/2 reads v[0..3] of a radix-8 last stage and the compiler
+// drops the rest of that stage's butterfly.
+template <int P, bool INV, bool REV, bool LO_IN = false, class LAY0, class LAY1, class SYNC = CtaSync>
 __device__ __forceinline__ void reg_fft(float2 (&v)[8], float2* buf, const LAY0& lay0, const LAY1& lay1, int t,
                                         const float2* __restrict__ tws, const SYNC& sync = SYNC()) {
   typedef TwTable<P, REV> TT;
-  rstage<P, TT::R0, 1, INV>(v, t, tws);
+  rstage<P, TT::R0, 1, INV, LO_IN>(v, t, tws);
   rexchange<P, TT::R0, 1, TT::R1>(v, buf, lay0, t, sync);
   rstage<P, TT::R1, TT::R0, INV>(v, t, tws + TT::OFF1);
   if constexpr (RPlan<P>::NSTAGE == 3) {
