@@ -226,7 +226,8 @@ cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int r
  * loading the library holds until exit; calls needing more (16 bytes x 512
  * + 8 x nvec x n x P bytes) return CISOR_ERR_INVALID_ARG with a message.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  Every call
+ * (cudaGetSymbolAddress) and raises the convolution kernels' shared-memory
+ * limit (cudaFuncSetAttribute), so make it before any stream capture.  Every call
  * shares the array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller.  Each call rewrites
  * every scratch value it reads.  Asynchronous on `stream`. */

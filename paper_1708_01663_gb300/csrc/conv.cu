@@ -144,6 +144,24 @@ struct ColGeo {
   int tx_div;
 };
 
+// Dynamic shared memory of the column kernel, in float2: the exchange
+// buffers, the forward and reversed twiddle tables.  Three-stage plans
+// ping-pong their two exchanges between two buffers (one barrier per
+// exchange instead of two), which exceeds the 48 KB of static shared memory
+// at W P = 4096.  TWALL: with W >= 16 columns per CTA a warp's threads span at
+// most two twiddle indices, so reading all twiddle powers from the table
+// (broadcast reads) is cheaper than forming them by products.
+template <int P, int MODE, int NT> struct ColSmem {
+  static constexpr int W = ConvCfg<P>::template Col<NT>::W;
+  static constexpr bool PING = RPlan<P>::NSTAGE == 3;
+  static constexpr bool TWALL = W >= 16;
+  static constexpr int BUF = P * W;
+  static constexpr int BUF2 = PING ? P * W : 0;
+  static constexpr int TW = MODE == COL_INV ? 0 : TwTable<P, false>::SIZE;
+  static constexpr int TWR = MODE == COL_FWD ? 0 : TwTable<P, true>::SIZE;
+  static constexpr size_t BYTES = sizeof(float2) * (size_t)(BUF + BUF2 + TW + TWR);
+};
+
 // D3 = false (2D) fixes es = P and a single slab at compile time.
 template <int P, int MODE, bool ADJ, int NT, bool D3>
 __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict__ active, const float2* __restrict__ tw_g,
@@ -151,10 +169,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
                                                     const ColGeo geo) {
   typedef ConvCfg<P> C;
   typedef RPlan<P> PL;
-  __shared__ float2 tw[MODE == COL_INV ? 1 : TwTable<P, false>::SIZE];
-  __shared__ float2 twr[MODE == COL_FWD ? 1 : TwTable<P, true>::SIZE];
-  constexpr int W = C::template Col<NT>::W;
-  __shared__ float2 buf[P * W];
+  typedef ColSmem<P, MODE, NT> SM;
+  constexpr int W = SM::W;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* buf = smem;
+  float2* buf2 = buf + SM::BUF;
+  float2* tw = buf2 + SM::BUF2;
+  float2* twr = tw + SM::TW;
   const int tx = blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
@@ -185,7 +206,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
         const int i = PL::elem(lt, q, r, R0);
         v[q * R0 + r] = (PL::lower(q, r, R0) && i < n) ? base[i * es] : make_float2(0.f, 0.f);
       }
-    reg_fft<P, false, false, true>(v, buf, lay, lay, lt, tw);
+    reg_fft<P, false, false, true, SM::TWALL, SM::PING>(v, buf, lay, lay, lt, tw, CtaSync(), buf2);
   }
   constexpr int RL = PL::template last<false>();
   if (MODE == COL_FWD) {
@@ -207,7 +228,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
         v[q * RL + r] = c_mul(v[q * RL + r], g);
       }
   }
-  reg_fft<P, true, true>(v, buf, layr, layr, lt, twr);
+  // PING: both transforms use buf, then buf2, and each exchange's barrier orders the reads of
+  // the one before (reg_fft); otherwise the leading barrier of each exchange does
+  reg_fft<P, true, true, false, SM::TWALL, SM::PING>(v, buf, layr, layr, lt, twr, CtaSync(), buf2);
   constexpr int RI = PL::template last<true>();
 #pragma unroll
   for (int q = 0; q < 8 / RI; ++q)
@@ -336,16 +359,43 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
 template <int P, int MODE, bool ADJ, int NT>
 static void launch_cols(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
   constexpr int W = ConvCfg<P>::template Col<NT>::W;
+  constexpr size_t SMB = ColSmem<P, MODE, NT>::BYTES;
   const ColGeo geo{c->n, P / W, es, slab, c->rtstride, op.tx_div};
   dim3 g((P / W) * nslab, op.ntx);
   if constexpr (P <= 256) {  // 3D grids use P <= 256
     if (c->dim == 3) {
-      conv_cols<P, MODE, ADJ, NT, true><<<g, NT, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
+      conv_cols<P, MODE, ADJ, NT, true><<<g, NT, SMB, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
       return;
     }
   }
   if constexpr (MODE == COL_G)
-    conv_cols<P, MODE, ADJ, NT, false><<<g, NT, 0, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
+    conv_cols<P, MODE, ADJ, NT, false><<<g, NT, SMB, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
+}
+
+// The column kernels' dynamic shared memory may exceed the 48 KB default: raise
+// each instantiation's limit once, when a context picks its FFT size.
+template <int P, int MODE, bool ADJ, int NT, bool D3>
+static cudaError_t cols_attr() {
+  return cudaFuncSetAttribute(conv_cols<P, MODE, ADJ, NT, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ColSmem<P, MODE, NT>::BYTES);
+}
+template <int P, bool ADJ, int NT>
+static cudaError_t cols_attrs() {
+  cudaError_t e = cols_attr<P, COL_G, ADJ, NT, false>();
+  if constexpr (P <= 256) {
+    if (e == cudaSuccess) e = cols_attr<P, COL_G, ADJ, NT, true>();
+    if (e == cudaSuccess) e = cols_attr<P, COL_FWD, ADJ, NT, true>();
+    if (e == cudaSuccess) e = cols_attr<P, COL_INV, ADJ, NT, true>();
+  }
+  return e;
+}
+template <int P>
+static cisor_status conv_init_t() {
+  CISOR_CUDA((cols_attrs<P, false, 256>()));
+  CISOR_CUDA((cols_attrs<P, true, 256>()));
+  CISOR_CUDA((cols_attrs<P, false, 512>()));
+  CISOR_CUDA((cols_attrs<P, true, 512>()));
+  return CISOR_OK;
 }
 
 template <int P, int MODE>
@@ -412,10 +462,10 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
 
 cisor_status conv_init(int P) {
   switch (P) {
-    case 64:
-    case 128:
-    case 256:
-    case 512: return CISOR_OK;
+    case 64: return conv_init_t<64>();
+    case 128: return conv_init_t<128>();
+    case 256: return conv_init_t<256>();
+    case 512: return conv_init_t<512>();
   }
   set_error("unsupported FFT size %d", P);
   return CISOR_ERR_INVALID_ARG;

@@ -88,17 +88,31 @@ template <int P, bool REV> struct TwTable {
 };
 constexpr int TW_STRIDE = 512;  // floats2 reserved per plan table
 
-// One stage on the thread's registers.  Only w = tws[k] (the r = 1 row of
-// the stage table) is read from shared memory; w^2 .. w^7 are formed by
-// complex products (depth 3), trading shared-memory loads for FMAs.  LO: the
+// a * conj(b)
+__device__ __forceinline__ float2 c_mulcj(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// One stage on the thread's registers.  TWALL = false: only w = tws[k] (the
+// r = 1 row of the stage table) is read from shared memory and w^2 .. w^7 are
+// formed by complex products (depth 3), trading shared-memory loads for FMAs;
+// TWALL = true: all R - 1 powers are read from the table (the better trade
+// where a warp's threads share few k, so each read is a broadcast).  LO: the
 // upper half of each radix-8 input group is zero (first stage only).
-template <int P, int R, int NS, bool INV, bool LO = false>
+template <int P, int R, int NS, bool INV, bool LO = false, bool TWALL = false>
 __device__ __forceinline__ void rstage(float2 (&v)[8], int t, const float2* __restrict__ tws) {
   static_assert(!LO || (R == 8 && NS == 1), "pruned inputs only in a radix-8 first stage");
   constexpr int NTF = P / 8;
 #pragma unroll
   for (int q = 0; q < 8 / R; ++q) {
-    if constexpr (NS > 1) {
+    if constexpr (NS > 1 && TWALL) {
+      const int k = (t + q * NTF) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tws[(r - 1) * NS + k];
+        v[q * R + r] = INV ? c_mulcj(v[q * R + r], w) : c_mul(v[q * R + r], w);
+      }
+    } else if constexpr (NS > 1) {
       const int j = t + q * NTF;
       const int k = j & (NS - 1);
       float2 w1 = tws[k];
@@ -145,12 +159,14 @@ template <int P> struct RowSync {
   }
 };
 
-// outputs of a stage (radix RO, size NS) to shared memory, then the inputs of the next stage (radix RI)
-template <int P, int RO, int NS, int RI, class LAY, class SYNC = CtaSync>
+// outputs of a stage (radix RO, size NS) to shared memory, then the inputs of
+// the next stage (radix RI).  PRE: barrier before the writes, needed when an
+// earlier exchange read buf with no barrier since.
+template <int P, int RO, int NS, int RI, class LAY, class SYNC = CtaSync, bool PRE = true>
 __device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY& lay, int t,
                                           const SYNC& sync = SYNC()) {
   constexpr int NTF = P / 8;
-  sync();
+  if constexpr (PRE) sync();
 #pragma unroll
   for (int q = 0; q < 8 / RO; ++q) {
     const int j = t + q * NTF;
@@ -176,16 +192,25 @@ __device__ __forceinline__ void rexchange(float2 (&v)[8], float2* buf, const LAY
 // they are zero; the caller need not set them.  A caller that wants only the
 // outputs below P/2 reads v[0..3] of a radix-8 last stage and the compiler
 // drops the rest of that stage's butterfly.
-template <int P, bool INV, bool REV, bool LO_IN = false, class LAY0, class LAY1, class SYNC = CtaSync>
+// PING (three-stage plans): the second exchange goes through buf2, so neither
+// exchange needs a barrier before its writes.  The caller guarantees that
+// every read of buf by an earlier exchange is separated from this call by a
+// barrier; a three-stage PING transform followed by another one satisfies
+// this for both buffers (each exchange's barrier orders the reads of the
+// previous exchange, which used the other buffer).
+template <int P, bool INV, bool REV, bool LO_IN = false, bool TWALL = false, bool PING = false, class LAY0,
+          class LAY1, class SYNC = CtaSync>
 __device__ __forceinline__ void reg_fft(float2 (&v)[8], float2* buf, const LAY0& lay0, const LAY1& lay1, int t,
-                                        const float2* __restrict__ tws, const SYNC& sync = SYNC()) {
+                                        const float2* __restrict__ tws, const SYNC& sync = SYNC(),
+                                        float2* buf2 = nullptr) {
   typedef TwTable<P, REV> TT;
+  constexpr bool PP = PING && RPlan<P>::NSTAGE == 3;
   rstage<P, TT::R0, 1, INV, LO_IN>(v, t, tws);
-  rexchange<P, TT::R0, 1, TT::R1>(v, buf, lay0, t, sync);
-  rstage<P, TT::R1, TT::R0, INV>(v, t, tws + TT::OFF1);
+  rexchange<P, TT::R0, 1, TT::R1, LAY0, SYNC, !PP>(v, buf, lay0, t, sync);
+  rstage<P, TT::R1, TT::R0, INV, false, TWALL>(v, t, tws + TT::OFF1);
   if constexpr (RPlan<P>::NSTAGE == 3) {
-    rexchange<P, TT::R1, TT::R0, TT::R2>(v, buf, lay1, t, sync);
-    rstage<P, TT::R2, TT::R0 * TT::R1, INV>(v, t, tws + TT::OFF2);
+    rexchange<P, TT::R1, TT::R0, TT::R2, LAY1, SYNC, !PP>(v, PP ? buf2 : buf, lay1, t, sync);
+    rstage<P, TT::R2, TT::R0 * TT::R1, INV, false, TWALL>(v, t, tws + TT::OFF2);
   }
 }
 

@@ -24,7 +24,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 static std::mutex g_static_mu;
 static void* g_static_ptr[kMaxDevices];  // device address of g_static_scratch, per device
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device, looked up once
+// per device; the same first call raises the convolution kernels' dynamic
+// shared-memory limits for every supported FFT size.
 static cisor_status static_scratch_address(void** out) {
   int dev = 0;
   CISOR_CUDA(cudaGetDevice(&dev));
@@ -36,6 +38,7 @@ static cisor_status static_scratch_address(void** out) {
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
     CISOR_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    for (int P = 64; P <= 512; P *= 2) CISOR_TRY(conv_init(P));
     g_static_ptr[dev] = p;
   }
   *out = g_static_ptr[dev];
