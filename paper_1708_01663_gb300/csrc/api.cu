@@ -704,9 +704,16 @@ cisor_status cisor_set_rx_mask(cisor_ctx* c, const void* mask) {
   return call.leave();
 }
 
+static bool two_stage_ok(const cisor_ctx* c) { return c->dim == 2 && c->P == 512; }
+
 cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
-  if (!c || (cols_nt != 512 && cols_nt != 256)) {
-    set_error("cisor_set_cols_cta: NULL context or cols_nt not 512 / 256");
+  if (!c || (cols_nt != 512 && cols_nt != 256 && cols_nt != COLS_TWO_STAGE)) {
+    set_error("cisor_set_cols_cta: NULL context or cols_nt not 512 / 256 / %d", COLS_TWO_STAGE);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (cols_nt == COLS_TWO_STAGE && !two_stage_ok(c)) {
+    set_error("cisor_set_cols_cta: the two-stage column shape (%d) needs a 2D grid with P = 512 (this one: %dD, P = %d)",
+              COLS_TWO_STAGE, c->dim, c->P);
     return CISOR_ERR_INVALID_ARG;
   }
   if (cols_nt != c->cols_nt) {
@@ -744,11 +751,12 @@ cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   cudaEvent_t e0, e1;
   CISOR_CUDA(cudaEventCreate(&e0));
   CISOR_CUDA(cudaEventCreate(&e1));
-  const int variants[2] = {512, 256};
+  const int variants[3] = {512, 256, COLS_TWO_STAGE};
+  const int nvar = two_stage_ok(c) ? 3 : 2;
   int best = 512;
   float best_ms = 1e30f;
   cisor_status st = CISOR_OK;
-  for (int v = 0; v < 2 && st == CISOR_OK; ++v) {
+  for (int v = 0; v < nvar && st == CISOR_OK; ++v) {
     c->cols_nt = variants[v];
     st = matvec_once(c, 0, c->T, c->s, c->tv);  // warm-up
     CISOR_CUDA(cudaEventRecord(e0, c->stream));

@@ -135,7 +135,8 @@ struct cisor_ctx {
   double* sparams;  // device [2]: solve tolerance, iteration cap (read by the captured graphs)
   int graph_chunk;
   long long launches;       // kernels launched (graph replays add their kernel count)
-  int cols_nt;              // threads per CTA of the column-FFT kernel (512 or 256), set by the autotuner
+  int cols_nt;              // column-FFT kernel shape (512 or 256 threads of the three-stage kernel, or
+                            // COLS_TWO_STAGE), set by the autotuner
   long long graph_kernels[2];
   std::vector<int> last_iters[2];  // per-transmitter iterations of the last forward / adjoint solve
 };
@@ -186,6 +187,8 @@ struct ConvOp {
                           // model run as consecutive transforms; 0 or 1: one)
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
+// column shape code of the two-stage (32 x 16) column kernel, 2D P = 512 only
+constexpr int COLS_TWO_STAGE = 16;
 // EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);
 // EPI_CONV_ADD: out = conv + aux (aux may be null)
 enum { EPI_MATVEC = 0, EPI_RESID = 1, EPI_CONV_ADD = 2 };

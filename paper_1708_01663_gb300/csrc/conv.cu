@@ -241,6 +241,94 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
     }
 }
 
+// Two-stage column pass of a 2D P = 512 convolution (column shape COLS_TWO_STAGE):
+// 512 = 32 x 16, so each transform needs one shared-memory exchange instead of
+// the two of the 8 x 8 x 8 plan.  16 threads per column, 32 elements per
+// thread, W = 16 columns per 256-thread CTA.  Forward: radix 32 on elements
+// lt + 16 r (r >= 16 is padding), outputs to row 32 lt + k; radix 16 on items
+// j = lt + 16 q reading rows j + 32 r with twiddles tw[r j] (tw[m] =
+// exp(-2 pi i m / 512)); register 16 q + r then holds frequency
+// lt + 16 q + 32 r.  The spectrum product, then the reversed plan: radix 16 on
+// the same registers, outputs to row 16 j + r; radix 32 on rows lt + 16 r with
+// conj(tw[r lt]); output k < 16 is element lt + 16 k (the first n are kept).
+// A half-warp's 16 lanes share one row, so every exchange access is a
+// contiguous row segment (no bank conflicts) and every twiddle read is a
+// broadcast.  Two CTAs per SM (at most 128 registers a thread).
+
+// Compiler-only ordering point: memory accesses are not moved across it, which
+// keeps the loads of one butterfly group from being hoisted above the
+// arithmetic of the previous one (bounding live registers).  The loads it
+// orders are plain ones: read-only (non-coherent) loads may move across it.
+__device__ __forceinline__ void reorder_fence() { asm volatile("" ::: "memory"); }
+
+constexpr int W2S = 16;  // columns per CTA of the two-stage kernel
+
+template <bool ADJ>
+__global__ void __launch_bounds__(16 * W2S, 2) conv_cols_w512(const int* __restrict__ active, const float2* tw,
+                                                             const float2* ghat, float2* __restrict__ R,
+                                                             const ColGeo geo) {
+  constexpr int W = W2S;
+  constexpr int P = 512;
+  extern __shared__ __align__(16) float2 smem[];  // [P rows][W columns]
+  const int tx = blockIdx.y;
+  if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
+  const int n = geo.n;
+  const int w = threadIdx.x % W, lt = threadIdx.x / W;
+  const int c0 = blockIdx.x * W;
+  float2* base = R + tx * geo.tstride + c0 + w;
+  float2 v[32];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = lt + 16 * r;
+    v[r] = i < n ? base[i * P] : make_float2(0.f, 0.f);
+  }
+  dft32_lo<false>(v);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) smem[(32 * lt + k) * W + w] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int j = lt + 16 * q;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 x = smem[(j + 32 * r) * W + w];
+      v[16 * q + r] = r == 0 ? x : c_mul(x, tw[r * j]);
+    }
+    dft16<false>(v + 16 * q);
+    reorder_fence();
+  }
+  const float2* gcol = ghat + c0 + w;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      float2 g = gcol[(lt + 16 * q + 32 * r) * P];
+      if (ADJ) g.y = -g.y;
+      v[16 * q + r] = c_mul(v[16 * q + r], g);
+    }
+    dft16<true>(v + 16 * q);
+    reorder_fence();
+  }
+  __syncthreads();  // every read of the first exchange is done
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) smem[(16 * (lt + 16 * q) + r) * W + w] = v[16 * q + r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const float2 x = smem[(lt + 16 * r) * W + w];
+    v[r] = r == 0 ? x : c_mulcj(x, tw[r * lt]);
+    if (r % 8 == 7) reorder_fence();
+  }
+  dft32<true>(v);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int i = lt + 16 * k;
+    if (i < n) base[i * P] = v[k];
+  }
+}
+
 // Inner-product sets of the inverse-row epilogue.  The solver's three are
 // compiled with fixed operands; DOTS_ANY reads the operand codes of ConvOp.
 //   DOTS_RV : slot 0 <aux, y>               (<rhat, v>, v = A p)
@@ -391,6 +479,11 @@ static cudaError_t cols_attrs() {
 }
 template <int P>
 static cisor_status conv_init_t() {
+  if constexpr (P == 512) {
+    constexpr int smb = (int)(sizeof(float2) * P * W2S);
+    CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+    CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  }
   CISOR_CUDA((cols_attrs<P, false, 256>()));
   CISOR_CUDA((cols_attrs<P, true, 256>()));
   CISOR_CUDA((cols_attrs<P, false, 512>()));
@@ -398,8 +491,26 @@ static cisor_status conv_init_t() {
   return CISOR_OK;
 }
 
+// the two-stage kernel (2D, P = 512; the API admits the shape only there)
+template <int P>
+static void launch_cols_two_stage(cisor_ctx* c, const ConvOp& op) {
+  if constexpr (P == 512) {
+    const ColGeo geo{c->n, P / W2S, P, 0, c->rtstride, op.tx_div};
+    const dim3 g(P / W2S, op.ntx);
+    const size_t smb = sizeof(float2) * P * W2S;
+    if (op.adjoint)
+      conv_cols_w512<true><<<g, 16 * W2S, smb, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+    else
+      conv_cols_w512<false><<<g, 16 * W2S, smb, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+  }
+}
+
 template <int P, int MODE>
 static void cols_pass(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
+  if (MODE == COL_G && c->dim == 2 && c->cols_nt == COLS_TWO_STAGE) {
+    launch_cols_two_stage<P>(c, op);
+    return;
+  }
   if (c->cols_nt == 256) {
     if (op.adjoint)
       launch_cols<P, MODE, true, 256>(c, op, nslab, es, slab);

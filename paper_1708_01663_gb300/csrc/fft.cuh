@@ -98,6 +98,108 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8_lo(C* v) {
   v[7] = f_sub(e3, w3o);
 }
 
+// cos(pi m / 16) and sin(pi m / 16) for 0 <= m <= 16 (decimal expansions).
+__host__ __device__ constexpr double cos16(int m) {
+  return m > 8 ? -cos16(16 - m)
+               : (m == 0 ? 1.0
+                  : m == 1 ? 0.98078528040323044913
+                  : m == 2 ? 0.92387953251128675613
+                  : m == 3 ? 0.83146961230254523708
+                  : m == 4 ? 0.70710678118654752440
+                  : m == 5 ? 0.55557023301960222474
+                  : m == 6 ? 0.38268343236508977173
+                  : m == 7 ? 0.19509032201612826785
+                           : 0.0);
+}
+__host__ __device__ constexpr double sin16(int m) { return m > 8 ? cos16(m - 8) : cos16(8 - m); }
+
+// a * w32^m, w32 = exp(-+2 pi i / 32) (- forward, + inverse), 0 <= m < 16; m = 0 and
+// m = 8 (-+i) cost no multiplications
+template <bool INV, int M> __device__ __forceinline__ float2 mul_w32(float2 a) {
+  if constexpr (M == 0) {
+    return a;
+  } else if constexpr (M == 8) {
+    return f_rot<INV>(a);
+  } else {
+    constexpr float c = (float)cos16(M), s = INV ? (float)sin16(M) : -(float)sin16(M);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+// radix-16 = two radix-8 DFTs (even / odd inputs) joined by w16^k = w32^(2k), k = 0..7
+template <bool INV> __device__ __forceinline__ void dft16(float2* v) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+  const float2 t0 = o[0], t1 = mul_w32<INV, 2>(o[1]), t2 = mul_w32<INV, 4>(o[2]), t3 = mul_w32<INV, 6>(o[3]),
+               t4 = mul_w32<INV, 8>(o[4]), t5 = mul_w32<INV, 10>(o[5]), t6 = mul_w32<INV, 12>(o[6]),
+               t7 = mul_w32<INV, 14>(o[7]);
+  const float2 t[8] = {t0, t1, t2, t3, t4, t5, t6, t7};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = f_add(e[k], t[k]);
+    v[k + 8] = f_sub(e[k], t[k]);
+  }
+}
+
+// w32^k o[k] for k = 0..15 (compile-time exponents)
+template <bool INV> __device__ __forceinline__ void mul_w32_ramp(float2* o) {
+  o[1] = mul_w32<INV, 1>(o[1]);
+  o[2] = mul_w32<INV, 2>(o[2]);
+  o[3] = mul_w32<INV, 3>(o[3]);
+  o[4] = mul_w32<INV, 4>(o[4]);
+  o[5] = mul_w32<INV, 5>(o[5]);
+  o[6] = mul_w32<INV, 6>(o[6]);
+  o[7] = mul_w32<INV, 7>(o[7]);
+  o[8] = mul_w32<INV, 8>(o[8]);
+  o[9] = mul_w32<INV, 9>(o[9]);
+  o[10] = mul_w32<INV, 10>(o[10]);
+  o[11] = mul_w32<INV, 11>(o[11]);
+  o[12] = mul_w32<INV, 12>(o[12]);
+  o[13] = mul_w32<INV, 13>(o[13]);
+  o[14] = mul_w32<INV, 14>(o[14]);
+  o[15] = mul_w32<INV, 15>(o[15]);
+}
+
+// radix-32 = two radix-16 DFTs (even / odd inputs) joined by w32^k, k = 0..15
+template <bool INV> __device__ __forceinline__ void dft32(float2* v) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+  mul_w32_ramp<INV>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    v[k] = f_add(e[k], o[k]);
+    v[k + 16] = f_sub(e[k], o[k]);
+  }
+}
+
+// radix-32 DFT of inputs whose upper half v[16..31] is zero, split by output
+// parity (decimation in frequency): X_2m = DFT16(x)_m, X_2m+1 = DFT16(w32^r x_r)_m.
+template <bool INV> __device__ __forceinline__ void dft32_lo(float2* v) {
+  float2 a[16], b[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) a[r] = b[r] = v[r];
+  mul_w32_ramp<INV>(b);
+  dft16<INV>(a);
+  dft16<INV>(b);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    v[2 * m] = a[m];
+    v[2 * m + 1] = b[m];
+  }
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft_r(C* v) {
   if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);

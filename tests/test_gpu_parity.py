@@ -204,3 +204,42 @@ def test_solve_iterations_and_cols_cta():
     assert rel(u2, u) < 1e-5
     with pytest.raises(Exception):
         ctx.set_cols_cta(128)
+    with pytest.raises(Exception):
+        ctx.set_cols_cta(16)  # the two-stage shape exists for P = 512 only (here P = 128)
+
+
+@pytest.mark.parametrize("n,pad", [(256, 0), (96, 512)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_column_shapes_at_p512(n, pad, adjoint):
+    """Every column-kernel shape at P = 512 (the three-stage kernel at 512 and 256
+    threads, the two-stage 32 x 16 kernel) against the oracle's A / A^H; n = 96
+    leaves most of each padded column empty (ragged rows and columns)."""
+    ctx, prob = make(n, 3, 8, 0.75 * n / 8 + 1.0, pad=pad)
+    assert ctx.P == 512
+    f = synth.ellipse_phantom(n, 4, (0.0, 0.8), 7, imag=0.05)
+    x = synth.random_field(8, (3, n, n))
+    op = prob.AH if adjoint else prob.A
+    ys = {}
+    for shape in (512, 256, 16):
+        ctx.set_cols_cta(shape)
+        y = np.empty((3, n, n), np.complex64)
+        ctx.apply_A(c64(f), c64(x), y, adjoint=adjoint)
+        for t in range(3):
+            assert rel(y[t], op(f, x[t])) < 2e-5, shape
+        ys[shape] = y
+    assert rel(ys[16], ys[512]) < 1e-5
+
+
+def test_two_stage_shape_solves_and_autotunes():
+    """Forward solves with the two-stage column kernel converge to the oracle's
+    fields, and the autotuner may pick any of the three shapes at P = 512."""
+    n = 256
+    ctx, prob = make(n, 2, 8, 0.75 * n / 8 + 1.5)
+    f = synth.ellipse_phantom(n, 5, (0.0, 0.3), 21)
+    ctx.set_cols_cta(16)
+    u = np.empty((2, n, n), np.complex64)
+    st, info = ctx.forward(c64(f), u_out=u, tol=1e-6, max_iter=3000)
+    assert info.resid_max <= 1e-6
+    ref, its, res = solve.solve_fields(prob, f, prob.u_in, tol=1e-12)
+    assert rel(u, ref) < 1e-4
+    assert ctx.autotune(reps=2) in (512, 256, 16)
