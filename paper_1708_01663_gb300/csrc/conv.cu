@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
 // conj(tw[r lt]); output k < 16 is element lt + 16 k (the first n are kept).
 // A half-warp's 16 lanes share one row, so every exchange access is a
 // contiguous row segment (no bank conflicts) and every twiddle read is a
-// broadcast.  Two CTAs per SM (at most 128 registers a thread).
+// broadcast (the 512-entry table is copied to shared memory first: read from
+// global memory the twiddles cost 6 % more time).  Two CTAs per SM (at most
+// 128 registers a thread).
 
 // Compiler-only ordering point: memory accesses are not moved across it, which
 // keeps the loads of one butterfly group from being hoisted above the
@@ -262,9 +264,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
 __device__ __forceinline__ void reorder_fence() { asm volatile("" ::: "memory"); }
 
 constexpr int W2S = 16;  // columns per CTA of the two-stage kernel
+// dynamic shared memory: the [512][W2S] exchange buffer, then the 512 twiddles
+constexpr size_t W2S_SMEM = sizeof(float2) * (512 * W2S + 512);
 
 template <bool ADJ>
-__global__ void __launch_bounds__(16 * W2S, 2) conv_cols_w512(const int* __restrict__ active, const float2* tw,
+__global__ void __launch_bounds__(16 * W2S, 2) conv_cols_w512(const int* __restrict__ active, const float2* tw_g,
                                                              const float2* ghat, float2* __restrict__ R,
                                                              const ColGeo geo) {
   constexpr int W = W2S;
@@ -276,6 +280,10 @@ __global__ void __launch_bounds__(16 * W2S, 2) conv_cols_w512(const int* __restr
   const int w = threadIdx.x % W, lt = threadIdx.x / W;
   const int c0 = blockIdx.x * W;
   float2* base = R + tx * geo.tstride + c0 + w;
+  // the twiddle table in shared memory (read after the first barrier)
+  float2* tws = smem + P * W;
+  for (int i = threadIdx.x; i < P; i += 16 * W) tws[i] = tw_g[i];
+  const float2* tw = tws;
   float2 v[32];
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
@@ -480,7 +488,7 @@ static cudaError_t cols_attrs() {
 template <int P>
 static cisor_status conv_init_t() {
   if constexpr (P == 512) {
-    constexpr int smb = (int)(sizeof(float2) * P * W2S);
+    constexpr int smb = (int)W2S_SMEM;
     CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
     CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
   }
@@ -497,7 +505,7 @@ static void launch_cols_two_stage(cisor_ctx* c, const ConvOp& op) {
   if constexpr (P == 512) {
     const ColGeo geo{c->n, P / W2S, P, 0, c->rtstride, op.tx_div};
     const dim3 g(P / W2S, op.ntx);
-    const size_t smb = sizeof(float2) * P * W2S;
+    const size_t smb = W2S_SMEM;
     if (op.adjoint)
       conv_cols_w512<true><<<g, 16 * W2S, smb, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
     else

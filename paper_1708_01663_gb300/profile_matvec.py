@@ -3,10 +3,11 @@
     python -m paper_1708_01663_gb300.profile_matvec --config c2 --reps 3
 
 Builds the tables of a named workload (seeded phantom, all transmitters, or
-the first ``--T``), autotunes the column-FFT tile (2 variants x (1 + 5)
-passes) and runs one untimed plus ``reps`` timed passes of y_t = A x_t over
-every transmitter through cisor_time_matvec.  ``--cols-cta 512|256`` sets
-the column-kernel shape instead of measuring it, so that no convolution runs
+the first ``--T``), autotunes the column-kernel shape (2 or 3 variants x
+(1 + 5) passes) and runs one untimed plus ``reps`` timed passes of
+y_t = A x_t over every transmitter through cisor_time_matvec.
+``--cols-cta 512|256|16`` sets the column-kernel shape instead of measuring
+it (16: the two-stage kernel, 2D P = 512), so that no convolution runs
 before the untimed pass and ``ncu -k regex:conv_ -c k`` (k = 3 kernels per
 pass in 2D, 5 in 3D) captures exactly that pass.
 """
@@ -24,7 +25,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--T", type=int, default=None)
-    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 256, 512])
+    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 16, 256, 512])
     args = ap.parse_args()
     import torch
 
