@@ -1,7 +1,7 @@
 // Learned warm start for the field solves: a Fourier neural operator (FNO)
 // that predicts the scattered field u - u_in from (f, u_in), trained on
 // fields the solver itself produces.  Not part of the paper; the plain solve
-// stays the fallback and the judge of convergence (the prediction is only an
+// stays the fallback and still decides convergence (the prediction is only an
 // initial guess x0 for A u = u_in).
 //
 // Network (grid 128 x 128, width 32, 16 modes, 4 Fourier layers, hidden 128):
