@@ -236,12 +236,13 @@ cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const 
 
 /* Autotuner of the FFT convolution's column-kernel shape: times the
  * three-stage (8 x 8 x 8 at P = 512) column kernel with 512- and 256-thread
- * CTAs (8 or 4 columns per CTA at P = 512) and, on 2D grids with P = 512, the
- * two-stage (32 x 16) kernel (shape code 16: 16 threads per column, 16
- * columns per CTA), on this context's sizes, `reps` batched matvecs each with
- * CUDA events, and keeps the fastest.  *cols_nt_out (may be NULL) receives
- * the chosen shape code (512, 256 or 16).  Results agree to FP32 rounding
- * whichever shape runs. */
+ * CTAs (8 or 4 columns per CTA at P = 512) and, where it exists, the
+ * two-stage kernel (shape code 16: one shared-memory exchange per transform;
+ * 512 = 32 x 16 on 2D grids, 256 = 16 x 16 and 128 = 16 x 8 on 2D and 3D
+ * grids; none at P = 64), on this context's sizes, `reps` batched matvecs
+ * each with CUDA events, and keeps the fastest.  *cols_nt_out (may be NULL)
+ * receives the chosen shape code (512, 256 or 16).  Results agree to FP32
+ * rounding whichever shape runs. */
 cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
 
 /* Per-transmitter receiver mask (the Fresnel set-ups of Sec. IV record each
@@ -253,8 +254,8 @@ cisor_status cisor_set_rx_mask(cisor_ctx* ctx, const void* mask);
 
 /* Set the column-kernel shape instead of measuring it, for reproducible
  * profiles: 512 or 256 (threads per CTA of the three-stage kernel) or 16 (the
- * two-stage kernel; 2D grids with P = 512 only, CISOR_ERR_INVALID_ARG
- * elsewhere).  Drops the captured solver graphs. */
+ * two-stage kernel; P = 128 or 256, or P = 512 on a 2D grid;
+ * CISOR_ERR_INVALID_ARG elsewhere).  Drops the captured solver graphs. */
 cisor_status cisor_set_cols_cta(cisor_ctx* ctx, int cols_nt);
 
 /* Per-transmitter BiCGSTAB iterations of the last forward (adjoint = 0) or

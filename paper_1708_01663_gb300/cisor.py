@@ -224,7 +224,7 @@ class Cisor:
         self.Nf = self.N * getattr(self, "ncomp", 1)  # field length per transmitter
 
     def autotune(self, reps=5):
-        """Time the column-kernel shapes (512, 256; 16 = two-stage on 2D P = 512) and keep the fastest."""
+        """Time the column-kernel shapes (512, 256; 16 = two-stage, P = 128 / 256 / 2D 512) and keep the fastest."""
         nt = c_int()
         _check(self._lib.cisor_autotune(self._ctx, int(reps), ctypes.byref(nt)))
         return nt.value
@@ -239,7 +239,7 @@ class Cisor:
         return _check(self._lib.cisor_set_rx_mask(self._ctx, m.ctypes.data_as(c_void_p)))
 
     def set_cols_cta(self, nt):
-        """Column-kernel shape: 512 or 256 threads of the three-stage kernel, or 16 (two-stage, 2D P = 512)."""
+        """Column-kernel shape: 512 or 256 threads of the three-stage kernel, or 16 (two-stage; P = 128, 256, 2D 512)."""
         return _check(self._lib.cisor_set_cols_cta(self._ctx, int(nt)))
 
     def solve_iterations(self, adjoint=False):

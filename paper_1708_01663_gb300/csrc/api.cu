@@ -704,7 +704,7 @@ cisor_status cisor_set_rx_mask(cisor_ctx* c, const void* mask) {
   return call.leave();
 }
 
-static bool two_stage_ok(const cisor_ctx* c) { return c->dim == 2 && c->P == 512; }
+static bool two_stage_ok(const cisor_ctx* c) { return c->P == 128 || c->P == 256 || (c->dim == 2 && c->P == 512); }
 
 cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
   if (!c || (cols_nt != 512 && cols_nt != 256 && cols_nt != COLS_TWO_STAGE)) {
@@ -712,8 +712,8 @@ cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
     return CISOR_ERR_INVALID_ARG;
   }
   if (cols_nt == COLS_TWO_STAGE && !two_stage_ok(c)) {
-    set_error("cisor_set_cols_cta: the two-stage column shape (%d) needs a 2D grid with P = 512 (this one: %dD, P = %d)",
-              COLS_TWO_STAGE, c->dim, c->P);
+    set_error("cisor_set_cols_cta: the two-stage column shape (%d) needs P = 128 or 256, or P = 512 in 2D "
+              "(this grid: %dD, P = %d)", COLS_TWO_STAGE, c->dim, c->P);
     return CISOR_ERR_INVALID_ARG;
   }
   if (cols_nt != c->cols_nt) {

@@ -187,7 +187,7 @@ struct ConvOp {
                           // model run as consecutive transforms; 0 or 1: one)
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
-// column shape code of the two-stage (32 x 16) column kernel, 2D P = 512 only
+// column shape code of the two-stage column kernels (P = 128, 256; P = 512 in 2D)
 constexpr int COLS_TWO_STAGE = 16;
 // EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);
 // EPI_CONV_ADD: out = conv + aux (aux may be null)

@@ -241,21 +241,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
     }
 }
 
-// Two-stage column pass of a 2D P = 512 convolution (column shape COLS_TWO_STAGE):
-// 512 = 32 x 16, so each transform needs one shared-memory exchange instead of
-// the two of the 8 x 8 x 8 plan.  16 threads per column, 32 elements per
-// thread, W = 16 columns per 256-thread CTA.  Forward: radix 32 on elements
-// lt + 16 r (r >= 16 is padding), outputs to row 32 lt + k; radix 16 on items
-// j = lt + 16 q reading rows j + 32 r with twiddles tw[r j] (tw[m] =
-// exp(-2 pi i m / 512)); register 16 q + r then holds frequency
-// lt + 16 q + 32 r.  The spectrum product, then the reversed plan: radix 16 on
-// the same registers, outputs to row 16 j + r; radix 32 on rows lt + 16 r with
-// conj(tw[r lt]); output k < 16 is element lt + 16 k (the first n are kept).
-// A half-warp's 16 lanes share one row, so every exchange access is a
-// contiguous row segment (no bank conflicts) and every twiddle read is a
-// broadcast (the 512-entry table is copied to shared memory first: read from
-// global memory the twiddles cost 6 % more time).  Two CTAs per SM (at most
-// 128 registers a thread).
+// Two-stage column kernels (column shape COLS_TWO_STAGE): P = E x NT with E
+// elements a thread and NT threads a column (512 = 32 x 16, 256 = 16 x 16,
+// 128 = 16 x 8), so each transform needs one shared-memory exchange instead of
+// the two of the three-stage plans.  The second radix equals NT, and with j
+// the item, lt the thread's place in its column and tw[m] = exp(-2 pi i m / P):
+//  forward : radix E on elements lt + NT r (r >= E/2 is padding when the
+//            input has n <= P/2 rows), outputs to row E lt + k; radix NT on
+//            items j = lt + NT q (q < E / NT) reading rows j + E r with
+//            twiddles tw[r j]; register NT q + r then holds frequency
+//            lt + NT q + E r;
+//  inverse : (the reversed plan, on those registers) radix NT in place,
+//            outputs to row NT j + r; radix E on rows lt + NT r with
+//            conj(tw[r lt]); output k is element lt + NT k, k < E/2 kept.
+// Modes as for conv_cols: COL_G (forward, ghat product, inverse), COL_FWD
+// (forward, all P outputs stored), COL_INV (inverse of all P inputs).
+// W = 256 / NT columns per 256-thread CTA: a half-warp's lanes share one row,
+// so every exchange access is a contiguous row segment (no bank conflicts) and
+// the twiddle reads, from a copy of the table in shared memory, are
+// broadcasts.  E = 32 takes 128 registers (2 CTAs per SM), E = 16 about 64.
+template <int P> struct TwoStage {
+  static constexpr int E = P == 512 ? 32 : 16;
+  static constexpr int NT = P / E;
+  static constexpr int Q = E / NT;
+  static constexpr int W = 256 / NT;
+  static constexpr int MINB = E == 32 ? 2 : 3;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)(P * W + P);  // exchange buffer, then twiddles
+  static_assert(P == 128 || P == 256 || P == 512, "two-stage plans: P = 128, 256, 512");
+};
 
 // Compiler-only ordering point: memory accesses are not moved across it, which
 // keeps the loads of one butterfly group from being hoisted above the
@@ -263,77 +276,93 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
 // orders are plain ones: read-only (non-coherent) loads may move across it.
 __device__ __forceinline__ void reorder_fence() { asm volatile("" ::: "memory"); }
 
-constexpr int W2S = 16;  // columns per CTA of the two-stage kernel
-// dynamic shared memory: the [512][W2S] exchange buffer, then the 512 twiddles
-constexpr size_t W2S_SMEM = sizeof(float2) * (512 * W2S + 512);
-
-template <bool ADJ>
-__global__ void __launch_bounds__(16 * W2S, 2) conv_cols_w512(const int* __restrict__ active, const float2* tw_g,
-                                                             const float2* ghat, float2* __restrict__ R,
-                                                             const ColGeo geo) {
-  constexpr int W = W2S;
-  constexpr int P = 512;
-  extern __shared__ __align__(16) float2 smem[];  // [P rows][W columns]
+template <int P, int MODE, bool ADJ, bool D3>
+__global__ void __launch_bounds__(256, TwoStage<P>::MINB)
+    conv_cols_2s(const int* __restrict__ active, const float2* tw_g, const float2* ghat, float2* __restrict__ R,
+                 const ColGeo geo) {
+  typedef TwoStage<P> TS;
+  constexpr int E = TS::E, NT = TS::NT, Q = TS::Q, W = TS::W;
+  extern __shared__ __align__(16) float2 smem[];  // [P rows][W columns], then P twiddles
   const int tx = blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
   const int w = threadIdx.x % W, lt = threadIdx.x / W;
-  const int c0 = blockIdx.x * W;
-  float2* base = R + tx * geo.tstride + c0 + w;
-  // the twiddle table in shared memory (read after the first barrier)
+  const int j3 = D3 ? blockIdx.x / geo.cps : 0;
+  const int c0 = (D3 ? blockIdx.x % geo.cps : blockIdx.x) * W;
+  const long long es = D3 ? geo.es : P;
+  float2* base = R + tx * geo.tstride + j3 * geo.slab + c0 + w;
+  // the twiddle table in shared memory (first read after a barrier); read from
+  // global memory it cost 6 % more time at P = 512
   float2* tws = smem + P * W;
-  for (int i = threadIdx.x; i < P; i += 16 * W) tws[i] = tw_g[i];
+  for (int i = threadIdx.x; i < P; i += 256) tws[i] = tw_g[i];
   const float2* tw = tws;
-  float2 v[32];
+  float2 v[E];
+  if constexpr (MODE != COL_INV) {
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int i = lt + 16 * r;
-    v[r] = i < n ? base[i * P] : make_float2(0.f, 0.f);
+    for (int r = 0; r < E / 2; ++r) {
+      const int i = lt + NT * r;
+      v[r] = i < n ? base[i * es] : make_float2(0.f, 0.f);
+    }
+    dft_n_lo<E, false>(v);
+#pragma unroll
+    for (int k = 0; k < E; ++k) smem[(E * lt + k) * W + w] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = lt + NT * q;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        const float2 x = smem[(j + E * r) * W + w];
+        v[NT * q + r] = r == 0 ? x : c_mul(x, tw[r * j]);
+      }
+      dft_n<NT, false>(v + NT * q);
+      reorder_fence();
+    }
+    if constexpr (MODE == COL_FWD) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < NT; ++r) base[(lt + NT * q + E * r) * es] = v[NT * q + r];
+      return;
+    }
+    const float2* gcol = ghat + j3 * geo.slab + c0 + w;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        float2 g = gcol[(lt + NT * q + E * r) * es];
+        if (ADJ) g.y = -g.y;
+        v[NT * q + r] = c_mul(v[NT * q + r], g);
+      }
+      dft_n<NT, true>(v + NT * q);
+      reorder_fence();
+    }
+    __syncthreads();  // every read of the first exchange is done
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+#pragma unroll
+      for (int r = 0; r < NT; ++r) v[NT * q + r] = base[(lt + NT * q + E * r) * es];
+      dft_n<NT, true>(v + NT * q);
+      reorder_fence();
+    }
   }
-  dft32_lo<false>(v);
 #pragma unroll
-  for (int k = 0; k < 32; ++k) smem[(32 * lt + k) * W + w] = v[k];
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < NT; ++r) smem[(NT * (lt + NT * q) + r) * W + w] = v[NT * q + r];
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = lt + 16 * q;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const float2 x = smem[(j + 32 * r) * W + w];
-      v[16 * q + r] = r == 0 ? x : c_mul(x, tw[r * j]);
-    }
-    dft16<false>(v + 16 * q);
-    reorder_fence();
-  }
-  const float2* gcol = ghat + c0 + w;
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      float2 g = gcol[(lt + 16 * q + 32 * r) * P];
-      if (ADJ) g.y = -g.y;
-      v[16 * q + r] = c_mul(v[16 * q + r], g);
-    }
-    dft16<true>(v + 16 * q);
-    reorder_fence();
-  }
-  __syncthreads();  // every read of the first exchange is done
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int r = 0; r < 16; ++r) smem[(16 * (lt + 16 * q) + r) * W + w] = v[16 * q + r];
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const float2 x = smem[(lt + 16 * r) * W + w];
+  for (int r = 0; r < E; ++r) {
+    const float2 x = smem[(lt + NT * r) * W + w];
     v[r] = r == 0 ? x : c_mulcj(x, tw[r * lt]);
     if (r % 8 == 7) reorder_fence();
   }
-  dft32<true>(v);
+  dft_n<E, true>(v);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int i = lt + 16 * k;
-    if (i < n) base[i * P] = v[k];
+  for (int k = 0; k < E / 2; ++k) {
+    const int i = lt + NT * k;
+    if (i < n) base[i * es] = v[k];
   }
 }
 
@@ -487,10 +516,20 @@ static cudaError_t cols_attrs() {
 }
 template <int P>
 static cisor_status conv_init_t() {
-  if constexpr (P == 512) {
-    constexpr int smb = (int)W2S_SMEM;
-    CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
-    CISOR_CUDA(cudaFuncSetAttribute(conv_cols_w512<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  if constexpr (P >= 128) {
+    constexpr int smb = (int)TwoStage<P>::SMEM;
+    for (int adj = 0; adj < 2; ++adj) {
+      CISOR_CUDA(cudaFuncSetAttribute(adj ? conv_cols_2s<P, COL_G, true, false> : conv_cols_2s<P, COL_G, false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      if constexpr (P <= 256) {
+        CISOR_CUDA(cudaFuncSetAttribute(adj ? conv_cols_2s<P, COL_G, true, true> : conv_cols_2s<P, COL_G, false, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+        CISOR_CUDA(cudaFuncSetAttribute(adj ? conv_cols_2s<P, COL_FWD, true, true> : conv_cols_2s<P, COL_FWD, false, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+        CISOR_CUDA(cudaFuncSetAttribute(adj ? conv_cols_2s<P, COL_INV, true, true> : conv_cols_2s<P, COL_INV, false, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      }
+    }
   }
   CISOR_CUDA((cols_attrs<P, false, 256>()));
   CISOR_CUDA((cols_attrs<P, true, 256>()));
@@ -499,24 +538,32 @@ static cisor_status conv_init_t() {
   return CISOR_OK;
 }
 
-// the two-stage kernel (2D, P = 512; the API admits the shape only there)
-template <int P>
-static void launch_cols_two_stage(cisor_ctx* c, const ConvOp& op) {
-  if constexpr (P == 512) {
-    const ColGeo geo{c->n, P / W2S, P, 0, c->rtstride, op.tx_div};
-    const dim3 g(P / W2S, op.ntx);
-    const size_t smb = W2S_SMEM;
-    if (op.adjoint)
-      conv_cols_w512<true><<<g, 16 * W2S, smb, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
-    else
-      conv_cols_w512<false><<<g, 16 * W2S, smb, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+// the two-stage kernels (P = 128, 256 in 2D and 3D; P = 512 in 2D; the API
+// admits the shape only there)
+template <int P, int MODE, bool ADJ>
+static void launch_cols_2s(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
+  if constexpr (P >= 128) {
+    typedef TwoStage<P> TS;
+    const ColGeo geo{c->n, P / TS::W, es, slab, c->rtstride, op.tx_div};
+    const dim3 g((P / TS::W) * nslab, op.ntx);
+    if constexpr (P <= 256) {
+      if (c->dim == 3) {
+        conv_cols_2s<P, MODE, ADJ, true><<<g, 256, TS::SMEM, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+        return;
+      }
+    }
+    if constexpr (MODE == COL_G)
+      conv_cols_2s<P, MODE, ADJ, false><<<g, 256, TS::SMEM, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
   }
 }
 
 template <int P, int MODE>
 static void cols_pass(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
-  if (MODE == COL_G && c->dim == 2 && c->cols_nt == COLS_TWO_STAGE) {
-    launch_cols_two_stage<P>(c, op);
+  if (c->cols_nt == COLS_TWO_STAGE) {
+    if (op.adjoint)
+      launch_cols_2s<P, MODE, true>(c, op, nslab, es, slab);
+    else
+      launch_cols_2s<P, MODE, false>(c, op, nslab, es, slab);
     return;
   }
   if (c->cols_nt == 256) {

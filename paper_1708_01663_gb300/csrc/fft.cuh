@@ -200,6 +200,40 @@ template <bool INV> __device__ __forceinline__ void dft32_lo(float2* v) {
   }
 }
 
+// radix-16 DFT of inputs whose upper half v[8..15] is zero, split by output
+// parity: X_2m = DFT8(x)_m, X_2m+1 = DFT8(w16^r x_r)_m (w16^r = w32^(2r)).
+template <bool INV> __device__ __forceinline__ void dft16_lo(float2* v) {
+  float2 a[8], b[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) a[r] = v[r];
+  b[0] = v[0];
+  b[1] = mul_w32<INV, 2>(v[1]);
+  b[2] = mul_w32<INV, 4>(v[2]);
+  b[3] = mul_w32<INV, 6>(v[3]);
+  b[4] = mul_w32<INV, 8>(v[4]);
+  b[5] = mul_w32<INV, 10>(v[5]);
+  b[6] = mul_w32<INV, 12>(v[6]);
+  b[7] = mul_w32<INV, 14>(v[7]);
+  dft8<INV>(a);
+  dft8<INV>(b);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    v[2 * m] = a[m];
+    v[2 * m + 1] = b[m];
+  }
+}
+
+// DFT of N = 8, 16, 32 registers, and of N = 16, 32 registers whose upper half is zero
+template <int N, bool INV> __device__ __forceinline__ void dft_n(float2* v) {
+  if constexpr (N == 32) dft32<INV>(v);
+  else if constexpr (N == 16) dft16<INV>(v);
+  else dft8<INV>(v);
+}
+template <int N, bool INV> __device__ __forceinline__ void dft_n_lo(float2* v) {
+  if constexpr (N == 32) dft32_lo<INV>(v);
+  else dft16_lo<INV>(v);
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft_r(C* v) {
   if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);

@@ -7,7 +7,7 @@ the first ``--T``), autotunes the column-kernel shape (2 or 3 variants x
 (1 + 5) passes) and runs one untimed plus ``reps`` timed passes of
 y_t = A x_t over every transmitter through cisor_time_matvec.
 ``--cols-cta 512|256|16`` sets the column-kernel shape instead of measuring
-it (16: the two-stage kernel, 2D P = 512), so that no convolution runs
+it (16: the two-stage kernel), so that no convolution runs
 before the untimed pass and ``ncu -k regex:conv_ -c k`` (k = 3 kernels per
 pass in 2D, 5 in 3D) captures exactly that pass.
 """

@@ -204,18 +204,22 @@ def test_solve_iterations_and_cols_cta():
     assert rel(u2, u) < 1e-5
     with pytest.raises(Exception):
         ctx.set_cols_cta(128)
+    small, _ = make(20, 2, 8, 3.0)
+    assert small.P == 64
     with pytest.raises(Exception):
-        ctx.set_cols_cta(16)  # the two-stage shape exists for P = 512 only (here P = 128)
+        small.set_cols_cta(16)  # no two-stage plan at P = 64
 
 
-@pytest.mark.parametrize("n,pad", [(256, 0), (96, 512)])
+@pytest.mark.parametrize("n,pad,P", [(256, 0, 512), (96, 512, 512), (100, 0, 256), (40, 256, 256), (64, 0, 128),
+                                     (33, 128, 128)])
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_column_shapes_at_p512(n, pad, adjoint):
-    """Every column-kernel shape at P = 512 (the three-stage kernel at 512 and 256
-    threads, the two-stage 32 x 16 kernel) against the oracle's A / A^H; n = 96
-    leaves most of each padded column empty (ragged rows and columns)."""
+def test_column_shapes(n, pad, P, adjoint):
+    """Every column-kernel shape (the three-stage kernel at 512 and 256 threads,
+    the two-stage kernel: 32 x 16 at P = 512, 16 x 16 at 256, 16 x 8 at 128)
+    against the oracle's A / A^H; a padded n leaves most of each column empty
+    (ragged rows and columns)."""
     ctx, prob = make(n, 3, 8, 0.75 * n / 8 + 1.0, pad=pad)
-    assert ctx.P == 512
+    assert ctx.P == P
     f = synth.ellipse_phantom(n, 4, (0.0, 0.8), 7, imag=0.05)
     x = synth.random_field(8, (3, n, n))
     op = prob.AH if adjoint else prob.A
@@ -243,3 +247,5 @@ def test_two_stage_shape_solves_and_autotunes():
     ref, its, res = solve.solve_fields(prob, f, prob.u_in, tol=1e-12)
     assert rel(u, ref) < 1e-4
     assert ctx.autotune(reps=2) in (512, 256, 16)
+    with pytest.raises(Exception):
+        make(64, 1, 8, 6.0, complex_f=False)[0].set_cols_cta(8)
