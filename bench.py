@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 16, 256, 512],
+                    help="column-kernel shape instead of autotuning it (0: autotune); for launch lists "
+                         "taken under a profiler, whose replays change the autotuner's timings")
     return ap.parse_args()
 
 
@@ -310,7 +313,11 @@ def main():
                       vectorial=vec)
     if "rx_mask" in cfg:
         ctx.set_rx_mask(cfg["rx_mask"])
-    cols_nt = ctx.autotune(reps=10)  # pick the column-FFT CTA shape by measurement
+    if args.cols_cta:
+        ctx.set_cols_cta(args.cols_cta)
+        cols_nt = args.cols_cta
+    else:
+        cols_nt = ctx.autotune(reps=10)  # pick the column-kernel shape by measurement
 
     # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
     f_dev = torch.from_numpy(np.ascontiguousarray(f_true, dtype=np.complex64)).to(dev)
@@ -473,7 +480,7 @@ def main():
                        "l2": (f"working set > L2 (Krylov vectors 12 x {T * N * 8 / 2**20:.0f} MB)" if flush is None
                               else "L2 flushed between timed steps (512 MB write outside the timed windows)"),
                        "parallelism": "independent replicas" if ws > 1 else "single GPU",
-                       "autotuned_cols_cta": cols_nt,
+                       "cols_cta": cols_nt, "cols_cta_from": "flag" if args.cols_cta else "autotune",
                        "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
                        "fwd_iters_max": max(i["iters_max"] for i in step_infos) if step_infos else None,
                        "adj_iters_max": max(i["adj_iters_max"] for i in step_infos) if step_infos else None,
