@@ -139,6 +139,26 @@ def test_gradient(complex_f):
         assert rel(g.real, g_ref.real) < 5e-4
 
 
+@pytest.mark.parametrize("shape", [512, 16])
+def test_gradient_p512_shapes(shape):
+    """D and the gradient at P = 512 (n = 130: most of each padded row and column
+    empty) with the three-stage kernels and with the two-stage row and column
+    kernels; exercises every prologue, epilogue and dot set of the solves plus
+    the G^H v + z epilogue of the gradient."""
+    n, T, M = 130, 2, 24
+    ctx, prob = make(n, T, M, 0.75 * n / 8 + 1.5, complex_f=True)
+    assert ctx.P == 512
+    ctx.set_cols_cta(shape)
+    f = synth.ellipse_phantom(n, 3, (0.05, 0.3), 31, 0.02)
+    f_true = synth.ellipse_phantom(n, 3, (0.05, 0.35), 32, 0.02)
+    _, y, _, _ = grad.forward(prob, f_true, tol=1e-12)
+    D_ref, g_ref = grad.data_and_grad(prob, f, y, tol=1e-12)
+    g = np.empty((n, n), np.complex64)
+    D, st, info = ctx.grad(c64(f), c64(y), g, tol=1e-6, max_iter=3000)
+    assert abs(D - D_ref) / D_ref < 1e-4
+    assert rel(g, g_ref) < 5e-4
+
+
 @pytest.mark.parametrize("complex_f", [False, True])
 def test_tv_prox(complex_f):
     n = 64
