@@ -187,6 +187,37 @@ struct ConvOp {
                           // model run as consecutive transforms; 0 or 1: one)
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
+// Programmatic dependent launch (sm_90 and later): the solver chain's kernels
+// are launched with programmatic stream serialization, so a kernel's CTAs may
+// become resident while its predecessor's last CTAs still run.  Each such
+// kernel calls pdl_trigger() (its own dependents may launch once all of its
+// CTAs have started) and then pdl_wait(), which returns once the predecessor
+// grid has completed and its memory operations are visible, before touching
+// any global memory.  Both are no-ops for a kernel launched without the
+// attribute.  The wait is the hardware's grid dependency, not a spin loop, and
+// a predecessor never waits on its dependent.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#ifndef CISOR_PDL
+#define CISOR_PDL 1
+#endif
+// launch kernel k with programmatic stream serialization (see pdl_wait)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = CISOR_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+}
+
 // column shape code of the two-stage column kernels (P = 128, 256; P = 512 in 2D)
 constexpr int COLS_TWO_STAGE = 16;
 // EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   typedef RPlan<P> PL;
   __shared__ float2 tw[TwTable<P, false>::SIZE];
   __shared__ float2 buf[C::RB * C::PP];
+  pdl_trigger();
+  pdl_wait();
   const int tx = blockIdx.y;
   const int txs = op.tx_div > 1 ? tx / op.tx_div : tx;  // transmitter of this transform
   if (op.active && !op.active[txs]) return;
@@ -176,6 +178,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
   float2* buf2 = buf + SM::BUF;
   float2* tw = buf2 + SM::BUF2;
   float2* twr = tw + SM::TW;
+  pdl_trigger();
+  pdl_wait();
   const int tx = blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
@@ -283,6 +287,8 @@ __global__ void __launch_bounds__(256, TwoStage<P>::MINB)
   typedef TwoStage<P> TS;
   constexpr int E = TS::E, NT = TS::NT, Q = TS::Q, W = TS::W;
   extern __shared__ __align__(16) float2 smem[];  // [P rows][W columns], then P twiddles
+  pdl_trigger();
+  pdl_wait();
   const int tx = blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
@@ -396,6 +402,8 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   typedef RPlan<P> PL;
   __shared__ float2 tw[TwTable<P, true>::SIZE];
   __shared__ float2 buf[C::RB * C::PP];
+  pdl_trigger();
+  pdl_wait();
   const int tx = blockIdx.y;
   if (op.active && !op.active[op.tx_div > 1 ? tx / op.tx_div : tx]) return;
   const int n = geo.n;
@@ -489,12 +497,14 @@ static void launch_cols(cisor_ctx* c, const ConvOp& op, int nslab, long long es,
   dim3 g((P / W) * nslab, op.ntx);
   if constexpr (P <= 256) {  // 3D grids use P <= 256
     if (c->dim == 3) {
-      conv_cols<P, MODE, ADJ, NT, true><<<g, NT, SMB, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
+      (void)launch_pdl(conv_cols<P, MODE, ADJ, NT, true>, g, dim3(NT), SMB, c->stream, op.active, c->twst, c->ghat, c->R,
+                       geo);
       return;
     }
   }
   if constexpr (MODE == COL_G)
-    conv_cols<P, MODE, ADJ, NT, false><<<g, NT, SMB, c->stream>>>(op.active, c->twst, c->ghat, c->R, geo);
+    (void)launch_pdl(conv_cols<P, MODE, ADJ, NT, false>, g, dim3(NT), SMB, c->stream, op.active, c->twst, c->ghat, c->R,
+                     geo);
 }
 
 // The column kernels' dynamic shared memory may exceed the 48 KB default: raise
@@ -548,12 +558,14 @@ static void launch_cols_2s(cisor_ctx* c, const ConvOp& op, int nslab, long long 
     const dim3 g((P / TS::W) * nslab, op.ntx);
     if constexpr (P <= 256) {
       if (c->dim == 3) {
-        conv_cols_2s<P, MODE, ADJ, true><<<g, 256, TS::SMEM, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+        (void)launch_pdl(conv_cols_2s<P, MODE, ADJ, true>, g, dim3(256), TS::SMEM, c->stream, op.active, c->tw, c->ghat,
+                         c->R, geo);
         return;
       }
     }
     if constexpr (MODE == COL_G)
-      conv_cols_2s<P, MODE, ADJ, false><<<g, 256, TS::SMEM, c->stream>>>(op.active, c->tw, c->ghat, c->R, geo);
+      (void)launch_pdl(conv_cols_2s<P, MODE, ADJ, false>, g, dim3(256), TS::SMEM, c->stream, op.active, c->tw, c->ghat,
+                       c->R, geo);
   }
 }
 
@@ -586,9 +598,11 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
   const RowGeo rg{n, c->nrows, c->rslab, c->rtstride};
   dim3 grow((c->nrows + C::RB - 1) / C::RB, op.ntx);
   switch (op.prologue) {
-    case PRO_COPY: conv_rows_fwd<P, PRO_COPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg); break;
-    case PRO_PUPDATE: conv_rows_fwd<P, PRO_PUPDATE><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg); break;
-    default: conv_rows_fwd<P, PRO_AXPY><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg); break;
+    case PRO_COPY: (void)launch_pdl(conv_rows_fwd<P, PRO_COPY>, grow, dim3(256), 0, c->stream, op, c->twst, c->R, rg); break;
+    case PRO_PUPDATE:
+      (void)launch_pdl(conv_rows_fwd<P, PRO_PUPDATE>, grow, dim3(256), 0, c->stream, op, c->twst, c->R, rg);
+      break;
+    default: (void)launch_pdl(conv_rows_fwd<P, PRO_AXPY>, grow, dim3(256), 0, c->stream, op, c->twst, c->R, rg); break;
   }
   CISOR_CUDA(cudaGetLastError());
   if (c->dim == 3) {
@@ -603,7 +617,8 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
   }
   CISOR_CUDA(cudaGetLastError());
   const int dk = dots_kind(op);
-#define CISOR_ROWS_INV(E, D) conv_rows_inv<P, E, D><<<grow, 256, 0, c->stream>>>(op, c->twst, c->R, rg, c->nblk)
+#define CISOR_ROWS_INV(E, D) \
+  (void)launch_pdl(conv_rows_inv<P, E, D>, grow, dim3(256), 0, c->stream, op, c->twst, c->R, rg, c->nblk)
   switch (op.epilogue) {
     case EPI_MATVEC:
       if (dk == DOTS_NONE) CISOR_ROWS_INV(EPI_MATVEC, DOTS_NONE);

@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(32) bicg_scalar_kernel(int mode, int nblk, con
                                                          double* __restrict__ scal, int* __restrict__ active,
                                                          int* __restrict__ iters, int* __restrict__ txflag,
                                                          const double* __restrict__ params) {
+  pdl_trigger();
+  pdl_wait();
   const int t = blockIdx.x, lane = threadIdx.x;
   float d[2 * DOT_SLOTS];
 #pragma unroll
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int nrows, int 
                                                           const float2* __restrict__ p, const float2* __restrict__ s,
                                                           const float2* __restrict__ tv, float2* __restrict__ r,
                                                           const float2* __restrict__ rhat, float* __restrict__ part) {
+  pdl_trigger();
+  pdl_wait();
   const int t = blockIdx.y;
   if (!active[t]) return;
   const double2* sc = reinterpret_cast<const double2*>(scal) + (size_t)t * SC_STRIDE;
@@ -209,8 +213,8 @@ __global__ void __launch_bounds__(256) bicg_update_kernel(int n, int nrows, int 
 }
 
 static cisor_status scalar_step(cisor_ctx* c, int mode, int ntx) {
-  bicg_scalar_kernel<<<ntx, 32, 0, c->stream>>>(mode, c->nblk * c->ncomp, c->part, c->scal, c->active, c->iters,
-                                               c->txflag, c->sparams);
+  (void)launch_pdl(bicg_scalar_kernel, dim3(ntx), dim3(32), 0, c->stream, mode, c->nblk * c->ncomp,
+                   (const float*)c->part, c->scal, c->active, c->iters, c->txflag, (const double*)c->sparams);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return CISOR_OK;
@@ -263,8 +267,9 @@ static cisor_status residual_pass(cisor_ctx* c, int adjoint, const float2* b, co
 static cisor_status update_step(cisor_ctx* c, float2* x, int ntx) {
   const int RB = conv_rows_per_block(c->P);
   dim3 g(c->nblk * c->ncomp, ntx);
-  bicg_update_kernel<<<g, 256, 0, c->stream>>>(c->n, c->nrows * c->ncomp, RB, c->nblk * c->ncomp, c->active, c->scal,
-                                               x, c->p, c->s, c->tv, c->r, c->rhat, c->part);
+  (void)launch_pdl(bicg_update_kernel, g, dim3(256), 0, c->stream, c->n, c->nrows * c->ncomp, RB, c->nblk * c->ncomp,
+                   (const int*)c->active, (const double*)c->scal, x, (const float2*)c->p, (const float2*)c->s,
+                   (const float2*)c->tv, c->r, (const float2*)c->rhat, c->part);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 1;
   return scalar_step(c, SCM_RHO, ntx);
