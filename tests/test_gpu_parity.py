@@ -139,6 +139,21 @@ def test_gradient(complex_f):
         assert rel(g.real, g_ref.real) < 5e-4
 
 
+@pytest.mark.parametrize("n,P", [(100, 256), (64, 128)])
+def test_forward_two_stage_2d(n, P):
+    """Forward solves through the two-stage column kernels at P = 256 (16 x 16) and
+    P = 128 (16 x 8) in 2D reach the oracle's fields."""
+    ctx, prob = make(n, 3, 16, 0.75 * n / 8 + 1.5)
+    assert ctx.P == P
+    ctx.set_cols_cta(16)
+    f = synth.ellipse_phantom(n, 3, (0.1, 0.6), 41, 0.03)
+    u = np.empty((3, n, n), np.complex64)
+    st, info = ctx.forward(c64(f), u_out=u, tol=1e-6, max_iter=3000)
+    ref, _, _ = solve.solve_fields(prob, f, prob.u_in, tol=1e-12)
+    assert info.resid_max <= 1e-6
+    assert rel(u, ref) <= 1e-4
+
+
 @pytest.mark.parametrize("shape", [512, 16])
 def test_gradient_p512_shapes(shape):
     """D and the gradient at P = 512 (n = 130: most of each padded row and column
