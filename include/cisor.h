@@ -159,16 +159,20 @@ cisor_status cisor_grad(cisor_ctx* ctx, const void* f, const void* y, void* grad
                         const cisor_solve_opts* opts, cisor_solve_info* info);
 
 /* Forward half of cisor_grad, for reverse-mode use: solves A u_t = u_in,t
- * (Eq. 13), forms w_t = H diag(u_t) f - y_t and D (Eq. 7), and keeps u_t and
- * w_t in the context (the fields are the checkpoint the backward half
- * needs; [T, N] complex64 each).  D_out: host double (may be NULL). */
+ * (Eq. 13), forms w_t = H diag(u_t) f - y_t and D (Eq. 7), and keeps f, u_t
+ * and w_t in the context (the checkpoint the backward half needs; [N] and
+ * [T, N] complex64).  D_out: host double (may be NULL). */
 cisor_status cisor_data_term(cisor_ctx* ctx, const void* f, const void* y, double* D_out,
                              const cisor_solve_opts* opts, cisor_solve_info* info);
 
-/* Backward half of cisor_grad (Prop. 1): from the u_t, w_t of the last
+/* Backward half of cisor_grad (Prop. 1): from the f, u_t, w_t of the last
  * cisor_data_term on this context, solves A^H v_t = diag(f)^H H^H w_t and
  * writes g = sum_t conj(u_t) (H^H w_t + G^H v_t) to grad_out ([N] complex64).
- * CISOR_ERR_INVALID_ARG if no cisor_data_term preceded it. */
+ * Calls that only read f in between (cisor_apply_A, cisor_sense,
+ * cisor_tv_prox, cisor_autotune, cisor_time_matvec) leave the checkpoint
+ * intact.  CISOR_ERR_INVALID_ARG if no cisor_data_term preceded it, or if a
+ * call that overwrites u_t or w_t came after it (cisor_forward, cisor_grad,
+ * cisor_step, cisor_sense_adjoint, a batch solve on this context). */
 cisor_status cisor_data_backward(cisor_ctx* ctx, void* grad_out, const cisor_solve_opts* opts,
                                  cisor_solve_info* info);
 
@@ -206,6 +210,13 @@ cisor_status cisor_step_update(cisor_ctx* ctx, cisor_fista_state* st, const void
  * inside replayed CUDA graphs included).  *count is a host long long. */
 cisor_status cisor_launch_count(const cisor_ctx* ctx, long long* count);
 
+/* Arithmetic resources of CUDA device `device`, for roofline figures:
+ * *sm_count multiprocessors, *max_clock_khz their peak clock, *fp32_lanes
+ * FP32 FMA lanes per multiprocessor (128 on compute capability 10.x and 12.x,
+ * 64 on 9.0 and 8.0, else 0 = unknown), *cc compute capability x 10.  Any
+ * output pointer may be NULL.  No GPU work is launched. */
+cisor_status cisor_device_info(int device, int* sm_count, int* max_clock_khz, int* fp32_lanes, int* cc);
+
 /* Time `reps` back-to-back batched matvecs y_t = A x_t (adjoint = 0) or
  * A^H x_t (adjoint = 1) over all T transmitters of the context's workspace
  * (the FFT-convolution kernels of the field solves, Eq. 4), with CUDA events
@@ -221,7 +232,8 @@ cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int r
  *   ghat_scaled: device [P, P] complex64, the Green spectrum divided by P*P
  *                (cisor_green_spectrum's output / (P*P));
  *   f: device [n*n]; x, y: device [nvec, n*n] complex64; 8 <= n <= 256;
- *   P a power of two in [64, 512] with P >= 2n - 1; stream: cudaStream_t.
+ *   P a power of two in [64, 512] with P >= 2n - 1; stream: cudaStream_t of
+ *   the current device (a stream of another device: CISOR_ERR_INVALID_ARG).
  * Scratch lives in one file-scope device array of 16 MiB that every GPU
  * loading the library holds until exit; calls needing more (16 bytes x 512
  * + 8 x nvec x n x P bytes) return CISOR_ERR_INVALID_ARG with a message.

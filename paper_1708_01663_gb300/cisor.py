@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "cisor_set_rx_mask": [vp, vp],
         "cisor_solve_iterations": [vp, c_int, POINTER(c_int), POINTER(c_int)],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
+        "cisor_device_info": [i, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
         "cisor_data_term": [vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
@@ -158,6 +159,14 @@ def ptr(a, count=None, dtype="complex64"):
     if count is not None and arr.size != count:
         raise ValueError(f"expected {count} elements, got {arr.size}")
     return arr.ctypes.data
+
+
+def device_info(device=0):
+    """SM count, peak SM clock (kHz), FP32 lanes per SM and compute capability x 10 of a CUDA device."""
+    lib = load()
+    v = [c_int() for _ in range(4)]
+    _check(lib.cisor_device_info(int(device), *[ctypes.byref(x) for x in v]))
+    return {"sm_count": v[0].value, "max_clock_khz": v[1].value, "fp32_lanes": v[2].value, "cc": v[3].value}
 
 
 def apply_A_static(ghat_scaled, f, x, y, n, P, adjoint=False, stream=None):

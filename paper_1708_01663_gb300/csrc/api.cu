@@ -113,7 +113,6 @@ static cisor_status data_core(cisor_ctx* c, const cisor_solve_opts* o, double* D
   CISOR_CUDA(cudaMemcpyAsync(c->h_dsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaStreamSynchronize(c->stream));
   if (D) *D = c->h_dsum[0];
-  c->have_w = 1;
   return s1;
 }
 
@@ -150,6 +149,13 @@ static cisor_status adjoint_core(cisor_ctx* c, const cisor_solve_opts* o, double
   return s2;
 }
 
+// Prop. 1's backward half needs the u, w and f of the forward half.  f is
+// checkpointed by cisor_data_term in c->f_ck; u and w live in buffers that
+// cisor_forward, cisor_sense_adjoint, cisor_grad, cisor_step and the batch
+// solves overwrite, so those entry points drop the held state and a later
+// cisor_data_backward is refused instead of differentiating at another point.
+static void drop_data_term(cisor_ctx* c) { c->have_w = 0; }
+
 static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double gamma, const float2* s, float2* zstep,
                               double* D, cisor_solve_info* info) {
   cisor_solve_info li{};
@@ -169,7 +175,7 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf, c->f_ck};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -321,6 +327,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->gz, TN);
   ALLOC(c->f, Nb);
   ALLOC(c->fz, Nb);
+  ALLOC(c->f_ck, Nb);
   ALLOC(c->grad, Nb);
   ALLOC(c->work_n, Nb);
   ALLOC(c->Y, TM);
@@ -462,6 +469,7 @@ cisor_status cisor_forward(cisor_ctx* c, const void* f, const void* u_in, const 
   }
   Call call(c);
   CISOR_TRY(call.enter());
+  drop_data_term(c);  // the solve overwrites c->u
   const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   const float2* b = c->u_in;
@@ -512,6 +520,7 @@ cisor_status cisor_sense_adjoint(cisor_ctx* c, const void* f, const void* w, voi
   }
   Call call(c);
   CISOR_TRY(call.enter());
+  drop_data_term(c);  // c->w is overwritten
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   CISOR_TRY(call.in(c->w, w, sizeof(float2) * (size_t)c->T * c->M));
   CISOR_TRY(sense_adjoint(c, c->f, c->w, c->z, c->b, c->T));
@@ -532,6 +541,7 @@ cisor_status cisor_grad(cisor_ctx* c, const void* f, const void* y, void* grad_o
   CISOR_TRY(call.enter());
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
   CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
+  drop_data_term(c);  // u and w are recomputed at this f
   double D = 0.0;
   cisor_status st = grad_core(c, o, 0.0, nullptr, nullptr, &D, info);
   if (!solve_ok(st)) return st;
@@ -550,12 +560,15 @@ cisor_status cisor_data_term(cisor_ctx* c, const void* f, const void* y, double*
   if (!check_opts(o)) return CISOR_ERR_INVALID_ARG;
   Call call(c);
   CISOR_TRY(call.enter());
+  drop_data_term(c);
   CISOR_TRY(call.in(c->f, f, sizeof(float2) * c->N));
+  CISOR_CUDA(cudaMemcpyAsync(c->f_ck, c->f, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
   CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
   double D = 0.0;
   cisor_solve_info li{};
   cisor_status st = data_core(c, o, &D, &li);
   if (!solve_ok(st)) return st;
+  c->have_w = 1;
   if (D_out) *D_out = D;
   if (info) *info = li;
   CISOR_TRY(call.leave());
@@ -574,6 +587,8 @@ cisor_status cisor_data_backward(cisor_ctx* c, void* grad_out, const cisor_solve
   }
   Call call(c);
   CISOR_TRY(call.enter());
+  // other entry points may have written c->f since cisor_data_term (apply_A, sense, autotune, time_matvec)
+  CISOR_CUDA(cudaMemcpyAsync(c->f, c->f_ck, sizeof(float2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
   cisor_solve_info li{};
   cisor_status st = adjoint_core(c, o, 0.0, nullptr, nullptr, &li);
   if (!solve_ok(st)) return st;
@@ -673,6 +688,7 @@ cisor_status cisor_step(cisor_ctx* c, cisor_fista_state* st, const void* y, cons
   CISOR_TRY(call.in(c->yobs, y, sizeof(float2) * (size_t)c->T * c->M));
   CISOR_TRY(call.in(c->f, st->s, nb));       // gradient at s_k
   CISOR_TRY(call.in(c->work_n, st->f, nb));  // f_{k-1}
+  drop_data_term(c);  // u and w are recomputed at s_k
   double D = 0.0;
   cisor_status s1 = grad_core(c, o, st->gamma, c->f, c->fz, &D, info);
   if (!solve_ok(s1)) return s1;
@@ -789,6 +805,19 @@ cisor_status cisor_launch_count(const cisor_ctx* c, long long* count) {
     return CISOR_ERR_INVALID_ARG;
   }
   *count = c->launches;
+  return CISOR_OK;
+}
+
+cisor_status cisor_device_info(int device, int* sm_count, int* max_clock_khz, int* fp32_lanes, int* cc) {
+  int sms = 0, clk = 0, ma = 0, mi = 0;
+  CISOR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  CISOR_CUDA(cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, device));
+  CISOR_CUDA(cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, device));
+  CISOR_CUDA(cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, device));
+  if (sm_count) *sm_count = sms;
+  if (max_clock_khz) *max_clock_khz = clk;
+  if (fp32_lanes) *fp32_lanes = (ma == 10 || ma == 12) ? 128 : ((ma == 9 || (ma == 8 && mi == 0)) ? 64 : 0);
+  if (cc) *cc = 10 * ma + mi;
   return CISOR_OK;
 }
 

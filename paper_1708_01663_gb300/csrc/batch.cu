@@ -179,6 +179,7 @@ cisor_status cisor_batch_forward(cisor_batch* b, const void* const* f, void* con
   for (int i = 0; i < np; ++i) {
     cisor_ctx* c = b->ctx[i];
     const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
+    c->have_w = 0;  // this solve overwrites the u a cisor_data_term on the problem's context left
     CISOR_CUDA(cudaMemcpyAsync(c->f, f[i], sizeof(float2) * c->N, cudaMemcpyDefault, c->stream));
     if (o->x0_mode == 0 || !c->have_u)
       CISOR_CUDA(cudaMemcpyAsync(c->u, c->u_in, vb, cudaMemcpyDeviceToDevice, c->stream));
@@ -220,6 +221,7 @@ cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* 
   for (int i = 0; i < np; ++i) {
     cisor_ctx* c = b->ctx[i];
     const size_t vb = sizeof(float2) * (size_t)c->T * c->Nf;
+    c->have_w = 0;  // u and w of the problem's context are overwritten
     CISOR_CUDA(cudaMemcpyAsync(c->f, f[i], sizeof(float2) * c->N, cudaMemcpyDefault, c->stream));
     CISOR_CUDA(cudaMemcpyAsync(c->yobs, y[i], sizeof(float2) * (size_t)c->T * c->M, cudaMemcpyDefault, c->stream));
     if (o->x0_mode == 0 || !c->have_u)

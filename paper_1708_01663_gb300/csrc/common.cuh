@@ -110,7 +110,9 @@ struct cisor_ctx {
   // Krylov workspace, [T, N] each
   float2 *R, *r, *rhat, *p, *v, *s, *tv, *b;
   float2 *u, *vadj;   // last forward / adjoint solutions (warm starts)
-  int have_u, have_v, have_w;  // warm starts held; data_core's u and w held for the backward half
+  int have_u, have_v;  // warm starts held
+  int have_w;          // 1 from cisor_data_term until an entry point overwrites the u or w it left
+  float2* f_ck;        // [N] the point of the last cisor_data_term (its backward half's f)
   float2 *z, *gz;     // H^H w and z + G^H v
   float2 *f, *fz, *grad, *work_n;  // [N]
   float2 *Y, *w, *yobs;          // [T, M]

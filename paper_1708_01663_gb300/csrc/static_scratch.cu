@@ -26,10 +26,19 @@ static void* g_static_ptr[kMaxDevices];  // device address of g_static_scratch, 
 
 // Device address of the scratch array on the current device, looked up once
 // per device; the same first call raises the convolution kernels' dynamic
-// shared-memory limits for every supported FFT size.
-static cisor_status static_scratch_address(void** out) {
+// shared-memory limits for every supported FFT size.  A stream of another
+// device is rejected: the address and the kernel attributes are per device.
+static cisor_status static_scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   CISOR_CUDA(cudaGetDevice(&dev));
+  if (stream) {
+    int sdev = -1;
+    CISOR_CUDA(cudaStreamGetDevice(stream, &sdev));
+    if (sdev != dev) {
+      set_error("cisor_apply_A_static: the stream belongs to device %d but device %d is current", sdev, dev);
+      return CISOR_ERR_INVALID_ARG;
+    }
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal %d outside the %d devices this entry point supports", dev, kMaxDevices);
     return CISOR_ERR_INVALID_ARG;
@@ -66,7 +75,7 @@ extern "C" cisor_status cisor_apply_A_static(const void* ghat_scaled, const void
     return CISOR_ERR_INVALID_ARG;
   }
   void* base = nullptr;
-  CISOR_TRY(static_scratch_address(&base));
+  CISOR_TRY(static_scratch_address((cudaStream_t)stream, &base));
   // Host-side descriptor of the launch; nothing in it is allocated.
   cisor_ctx c{};
   c.n = n;

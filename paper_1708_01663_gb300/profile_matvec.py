@@ -8,8 +8,10 @@ the first ``--T``), autotunes the column-kernel shape (2 or 3 variants x
 y_t = A x_t over every transmitter through cisor_time_matvec.
 ``--cols-cta 512|256|16`` sets the column-kernel shape instead of measuring
 it (16: the two-stage kernel), so that no convolution runs
-before the untimed pass and ``ncu -k regex:conv_ -c k`` (k = 3 kernels per
-pass in 2D, 5 in 3D) captures exactly that pass.
+before the untimed pass and
+``ncu --clock-control none --metrics gpu__time_duration.sum -k regex:conv_ -c k``
+(k = 3 kernels per pass in 2D, 5 in 3D) lists exactly that pass; a full-metric
+capture names one kernel (``-k regex:conv_cols``) and one launch (``-c 1``).
 """
 from __future__ import annotations
 

@@ -75,3 +75,30 @@ def test_autograd_gpu_finite_differences():
             dm = data_term(ft - e, yt, ctx, tol=1e-7).item()
             fd = (dp - dm) / (2 * h)
             assert abs(fd - g.reshape(-1)[int(p)]) < 3e-2 * scale
+
+
+def test_backward_survives_calls_that_only_read_f():
+    """cisor_data_backward differentiates at the point of the last cisor_data_term (Prop. 1) even when
+    calls that overwrite the context's f come in between; calls that overwrite the kept u or w make it
+    refuse instead of differentiating at another point."""
+    _, ctx, prob, f, y = _setup(False)
+    from paper_1708_01663_gb300 import cisor
+    fc = c64(f)
+    D, _, _ = ctx.data_term(fc, c64(y), tol=1e-7)
+    other = c64(synth.ellipse_phantom(prob.n, 2, (0.0, 0.9), 77))
+    x = c64(synth.random_field(5, (ctx.T, prob.n, prob.n)))
+    out = np.empty_like(x)
+    ctx.apply_A(other, x, out)
+    ctx.autotune(reps=1)
+    ctx.tv_prox(other, np.empty_like(other), 1e-3, 5)
+    g = np.empty(fc.shape, np.complex64)
+    ctx.data_backward(g, tol=1e-7)
+    D_ref, g_ref = ograd.data_and_grad(prob, f, y, tol=1e-12)
+    assert abs(D - D_ref) / D_ref < 1e-4
+    assert rel(g.real, g_ref.real) < 5e-4
+    # a forward solve overwrites the kept fields: the backward is refused
+    ctx.data_term(fc, c64(y), tol=1e-7)
+    ctx.forward(other, tol=1e-5)
+    with pytest.raises(cisor.CisorError) as ei:
+        ctx.data_backward(g, tol=1e-7)
+    assert ei.value.status == cisor.ERR_INVALID_ARG

@@ -190,7 +190,7 @@ def test_tv_prox(complex_f):
     assert np.array_equal(x.real, np.clip(zc.real, 0.0, 0.9))
 
 
-def test_relaxed_fista_c1_reconstruction():
+def _c1_problem():
     cfg = synth.CONFIGS["c1"]
     n, T, M = cfg["n"], cfg["T"], cfg["M"]
     ctx, prob = make(n, T, M, cfg["rx_radius"])
@@ -200,19 +200,37 @@ def test_relaxed_fista_c1_reconstruction():
     sigma = np.linalg.norm(y_clean) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(y_clean.size)
     y = y_clean + sigma * e
     gamma = 1.0 / grad.born_hessian_norm(prob)
-    K = cfg["outer"]
-    ref, hist = fista.relaxed_fista(prob, y, np.zeros((n, n)), gamma, cfg["tau"], cfg["alpha"], K,
+    return cfg, ctx, prob, f_true, y, gamma
+
+
+def _fista_parity(alpha, K):
+    cfg, ctx, prob, f_true, y, gamma = _c1_problem()
+    n = cfg["n"]
+    ref, hist = fista.relaxed_fista(prob, y, np.zeros((n, n)), gamma, cfg["tau"], alpha, K,
                                     cfg["tv_iters"], tol=1e-11)
     f = np.zeros((n, n), np.complex64)
     s = np.zeros((n, n), np.complex64)
-    st = ctx.new_state(f, s, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0)
+    st = ctx.new_state(f, s, alpha, gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0)
     Ds = []
     for _ in range(K):
         ctx.step(st, c64(y), tol=1e-6, max_iter=3000)
         Ds.append(st.D)
     assert rel(Ds, hist) < 1e-3
     assert rel(f, ref) <= 1e-3
+    return f, f_true, hist
+
+
+def test_relaxed_fista_c1_reconstruction():
+    cfg = synth.CONFIGS["c1"]
+    f, f_true, _ = _fista_parity(cfg["alpha"], cfg["outer"])
     assert fista.recon_snr_db(f, f_true) > 3.0
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_relaxed_fista_ista_and_fista_ends(alpha):
+    """The two ends of the relaxation (Sec. III-A): alpha = 0 is ISTA (no momentum), alpha = 1 plain
+    FISTA; 10 steps of each on the C1 workload against the oracle's trajectory."""
+    _fista_parity(alpha, 10)
 
 
 def test_solve_iterations_and_cols_cta():
