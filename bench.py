@@ -41,9 +41,16 @@ if ROOT not in sys.path:
 
 METRIC = "LS field solves/s at residual 1e-4, learned vs cold start; % of HBM peak"
 UNIT = "solves/s"
-# FP32 arithmetic peak of a GB300 from its unit counts and maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _fp32_peak(device):
+    """FP32 FMA peak of the device from its attributes: SMs x FP32 lanes per SM x 2 flops x peak SM clock."""
+    from paper_1708_01663_gb300 import cisor
+    d = cisor.device_info(device)
+    lanes = d["fp32_lanes"] or 128
+    tf = d["sm_count"] * lanes * 2 * d["max_clock_khz"] * 1e3 / 1e12
+    return tf, {"sm_count": d["sm_count"], "fp32_lanes_per_sm": lanes, "max_sm_clock_mhz": d["max_clock_khz"] / 1e3,
+                "cc": d["cc"], "source": "cudaDeviceGetAttribute (MultiProcessorCount, ClockRate) via cisor_device_info"}
 
 
 def _args():
@@ -56,6 +63,10 @@ def _args():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tx-chunk", type=int, default=-1,
+                    help="transmitters per convolution launch instead of the autotuned chunk (0: all at once)")
+    ap.add_argument("--fno-train", type=int, default=2000, help="c4: training phantoms (32 samples each)")
+    ap.add_argument("--fno-minutes", type=float, default=2.0, help="c4: training time budget")
     ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 16, 256, 512],
                     help="column-kernel shape instead of autotuning it (0: autotune); for launch lists "
                          "taken under a profiler, whose replays change the autotuner's timings")
@@ -160,6 +171,105 @@ def _oracle_sample_solves(cfg, f_point, angles, rx, txs, tol):
                            f"{tol:g}, FP64 numpy BiCGSTAB, {sec:.1f} s"), [x.reshape(shape) for x in xs]
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(cfg_name, txs, tol, rounds, barrier, queue):
+    """One host process of the oracle baseline (spawned): for each of its transmitters builds the
+    single-transmitter FP64 problem and its measurements (untimed), then runs `rounds` timed rounds,
+    each a cold-start forward solve, residual, adjoint solve and gradient term (Prop. 1) per transmitter
+    to residual `tol`; every round starts at a barrier shared by all workers."""
+    from oracle import grad, model, vector
+    from paper_1708_01663_gb300 import synth
+    cfg, f_true, angles, rx = synth.make_inputs(cfg_name)
+    n, dim = cfg["n"], cfg["dim"]
+    s0 = _state0(f_true).astype(np.complex128)
+    ft = f_true.astype(np.complex128)
+    items = []
+    for t in txs:
+        noise = synth.complex_noise(cfg["seed"] + 100, (cfg["T"], cfg["M"]))[t]
+        if cfg.get("vectorial"):
+            tx = np.asarray(angles)[[t]]
+            prob = vector.VectorProblem(n, cfg["delta"], tx[:, :3], tx[:, 3:], rx)
+            u = vector.solve_fields(prob, ft, prob.u_in, 1e-6)
+            y = prob.sense(ft, u)
+        else:
+            prob = model.Problem(n, cfg["delta"], np.asarray(angles)[[t]], rx, dim=dim,
+                                 tx_kind=cfg.get("tx_kind", "plane"))
+            _, y, _, _ = grad.forward(prob, ft, 1e-6)
+        mask = cfg["rx_mask"][[t]] if "rx_mask" in cfg else None
+        y = y + np.linalg.norm(y) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(y.size) * noise[None]
+        items.append((prob, y, mask))
+    for _ in range(rounds):
+        barrier.wait()
+        t0 = time.perf_counter()
+        for prob, y, mask in items:
+            if cfg.get("vectorial"):
+                vector.data_and_grad(prob, s0, y, tol)
+            else:
+                grad.data_and_grad(prob, s0, y, tol, mask=mask)
+        queue.put((t0, time.perf_counter()))
+
+
+def _oracle_rounds(cfg_name, T, tol, rounds, workers=None):
+    """Timed rounds of the oracle baseline on the host cores: one spawned process per core, one
+    transmitter each (the first `workers` transmitters); returns (per-round wall seconds, workers)."""
+    import multiprocessing as mp
+    workers = max(1, min(workers or (os.cpu_count() or 1), T))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"  # one thread per process: the processes are the parallelism
+    try:
+        procs = [ctx.Process(target=_oracle_worker, args=(cfg_name, [w], tol, rounds, barrier, queue))
+                 for w in range(workers)]
+        for p in procs:
+            p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    walls = []
+    for _ in range(rounds):
+        marks = [queue.get(timeout=3600) for _ in range(workers)]
+        walls.append(max(m[1] for m in marks) - min(m[0] for m in marks))
+    for p in procs:
+        p.join()
+        if p.exitcode != 0:
+            raise RuntimeError(f"oracle worker exited with {p.exitcode}")
+    return walls, workers
+
+
+def _oracle_sample_note(cfg_name, cfg, workers, tol):
+    what = ("vectorial forward + adjoint solves and gradient term" if cfg.get("vectorial")
+            else "forward + adjoint solves and gradient term (Prop. 1)")
+    return (f"FP64 numpy oracle, {workers} spawned processes on {workers} host cores ({_cpu_model()}), one "
+            f"transmitter each (transmitters 0-{workers - 1} of {cfg['T']}): cold-start {what} at the step's "
+            f"state to residual {tol:g}; measurements from the oracle's own forward model of the phantom "
+            f"(residual 1e-6) plus 40 dB noise per transmitter; set-up untimed, rounds started at a barrier")
+
+
 def _graddiv_torch(C, delta):
     """Comparison only: the appendix's finite-difference grad-div of [B, 3, n, n, n] fields (zero outside)."""
     import torch
@@ -232,29 +342,25 @@ def _workload(name, cfg):
 
 
 def run_reference(args):
+    """The FP64 oracle as the reference arm: each step is one barrier-started round of cold-start
+    forward + adjoint solves (and the gradient term), one transmitter per host core."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from paper_1708_01663_gb300 import synth
-    cfg, f_true, angles, rx = synth.make_inputs(args.config)
-    s0 = _state0(f_true).astype(np.complex128)
-    times, solves = [], []
-    for k in range(args.warmup + args.steps):
-        t = k % cfg["T"]
-        nsolve, sec, note, _ = _oracle_sample_solves(cfg, s0, angles, rx, [t], args.tol)
-        if k >= args.warmup:
-            times.append(sec)
-            solves.append(nsolve)
-    total = sum(times)
-    value = sum(solves) / total
-    sample = "one cold-start forward field solve per step (transmitter k mod T)"
+    cfg = synth.make_inputs(args.config)[0]
+    walls, workers = _oracle_rounds(args.config, cfg["T"], args.tol, args.warmup + args.steps)
+    timed = walls[args.warmup:]
+    total = sum(timed)
+    value = 2 * workers * len(timed) / total
+    note = _oracle_sample_note(args.config, cfg, workers, args.tol)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": _workload(args.config, cfg), "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 numpy BiCGSTAB, cold start to 1e-4: " + sample},
+        "config": {"workload": _workload(args.config, cfg), "sample": note,
+                   "solves_per_step": 2 * workers, "same_config": True},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": note},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -288,10 +394,171 @@ def _traffic_summary(config):
         return None
 
 
+def run_c4(args):
+    """Learned vs cold start on the FNO workload: 128 x 128 grids at lambda/8 (FFT 256), 32 plane waves,
+    phantoms of 3-10 seeded ellipses with real contrast in [0, 0.8].  The network is trained first
+    (solver-generated fields of --fno-train phantoms, Adam for --fno-minutes; untimed); each timed step is
+    one held-out phantom solved twice to residual 1e-4: from the cold start (x0 = u_in) and from the
+    learned warm start (x0 = u_in + FNO(f, u_in), inference inside the timed region).  value = learned
+    solves/s; the cold figure sits beside it."""
+    import torch
+
+    from paper_1708_01663_gb300 import build, cisor, train_fno
+    build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T, n = train_fno.T, train_fno.N
+    ang, rx = train_fno.geometry()
+    ctx = cisor.Cisor(n, train_fno.DELTA, ang, rx)
+    cols_nt = ctx.autotune(reps=10)
+    t0 = time.time()
+    fs, usc, u_in = train_fno.generate(ctx, range(args.fno_train), dev)
+    t_gen = time.time() - t0
+    net = cisor.FNO(max_batch=T, seed=1714)
+    t0 = time.time()
+    steps, losses = train_fno.train(net, fs, usc, u_in, args.fno_minutes)
+    t_train = time.time() - t0
+    del fs, usc
+    u = torch.empty((T, n * n), dtype=torch.complex64, device=dev)
+    x0 = torch.empty_like(u)
+    held = list(range(100000, 100000 + args.warmup + args.steps))
+    fph = [torch.from_numpy(train_fno.phantom(i).astype(np.complex64).ravel()).to(dev) for i in held]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    cold_ms, warm_ms, inf_ms, ci, wi, pred = [], [], [], [], [], []
+    clocks = ClockSampler(local)
+    l0 = 0
+    for k, f in enumerate(fph):
+        if k == args.warmup:
+            torch.cuda.synchronize()
+            clocks.start()
+            l0 = ctx.launch_count()
+        ev[0].record()
+        _, ic = ctx.forward(f, u_out=u, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
+        ev[1].record()
+        u_ref = u.clone()
+        ev[2].record()
+        net.warm_start(ctx, f, x0)
+        ev[3].record()
+        torch.cuda.synchronize()
+        t_inf = ev[2].elapsed_time(ev[3])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.warm_start(ctx, f, x0)
+        _, iw = ctx.forward(f, x0=x0, u_out=u, tol=args.tol, max_iter=args.max_iter, x0_mode=1, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            cold_ms.append(ev[0].elapsed_time(ev[1]))
+            warm_ms.append(e0.elapsed_time(e1))
+            inf_ms.append(t_inf)
+            ci.append(ic.iters_mean)
+            wi.append(iw.iters_mean)
+            pred.append(float(torch.linalg.vector_norm(x0 - u_ref) / torch.linalg.vector_norm(u_ref - u_in)))
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    value = T * len(warm_ms) / (sum(warm_ms) / 1e3)
+    cold_value = T * len(cold_ms) / (sum(cold_ms) / 1e3)
+    # end to end through host buffers: f from pinned host memory, warm start, solve, fields back to the host
+    f_h = [f.cpu().pin_memory() for f in fph[:args.steps]]
+    u_h = torch.empty((T, n * n), dtype=torch.complex64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f in f_h:
+        fd = f.to(dev, non_blocking=True)
+        net.warm_start(ctx, fd, x0)
+        ctx.forward(fd, x0=x0, u_out=u_h, tol=args.tol, max_iter=args.max_iter, x0_mode=1, check=False)
+    torch.cuda.synchronize()
+    e2e = T * len(f_h) / (time.perf_counter() - t0)
+    mv_ms = ctx.time_matvec(fph[0], adjoint=False, reps=20)
+    Pd = ctx.P ** 2
+    alg_flops = T * 2 * 5 * Pd * np.log2(Pd)
+    alg_bytes = T * 16 * ctx.N + 8 * ctx.N
+    fp32_peak, peak_inputs = _fp32_peak(local)
+    hbm_peak, peak_kind = _peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(warm_ms), "warmup": args.warmup,
+        "ms_per_step": float(np.mean(warm_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (FNO: bf16 weights, fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": "c4: 128x128 at lambda/8, FFT 256x256, 32 plane waves, 64 Rx, 3-10 ellipses "
+                               "contrast [0, 0.8]; learned warm start (FNO: 4 Fourier layers, width 32, 16 modes)",
+                   "step": "one held-out phantom: 32 solves to residual 1e-4 from the learned warm start, "
+                           "inference included",
+                   "train_phantoms": args.fno_train, "train_samples": args.fno_train * T, "gen_s": t_gen,
+                   "train_s": t_train, "train_steps": steps, "loss_first": float(np.mean(losses[:20])),
+                   "loss_last": float(np.mean(losses[-50:])), "heldout_phantoms": len(warm_ms),
+                   "pred_rel_err_mean": float(np.mean(pred)), "cols_cta": cols_nt,
+                   "l2": "working set < L2: each timed phantom follows the previous phantom's solves"},
+        "learned_vs_cold": {"learned_solves_per_s": value, "cold_solves_per_s": cold_value,
+                            "time_saved_frac": 1.0 - float(np.mean(warm_ms)) / float(np.mean(cold_ms)),
+                            "cold_ms_per_phantom": float(np.mean(cold_ms)),
+                            "learned_ms_per_phantom": float(np.mean(warm_ms)),
+                            "inference_ms_per_phantom": float(np.mean(inf_ms)),
+                            "cold_iters_mean": float(np.mean(ci)), "learned_iters_mean": float(np.mean(wi)),
+                            "iters_saved_frac": 1.0 - float(np.mean(wi)) / float(np.mean(ci)),
+                            "cold_iters_p95": float(np.percentile(ci, 95)),
+                            "learned_iters_p95": float(np.percentile(wi, 95))},
+        "roofline": {"bound": "alu", "achieved": alg_flops / (mv_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": alg_flops / (mv_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+                     "kernel": "batched FFT matvec A x over all T", "ms_per_launch": mv_ms,
+                     "peak_inputs": peak_inputs,
+                     "hbm": {"achieved": alg_bytes / (mv_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": alg_bytes / (mv_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_kind": f"{peak_kind} copy bandwidth"}},
+        "cpu_baseline": None,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": T * n * n * 8},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        walls, workers = _oracle_rounds_c4(args.tol)
+        line["cpu_baseline"] = {"value": workers * len(walls) / sum(walls), "unit": UNIT, "cores": workers,
+                                "kind": "oracle",
+                                "sample": f"FP64 numpy oracle, {workers} spawned processes on {workers} host cores "
+                                          f"({_cpu_model()}): cold-start forward solves of held-out phantom 0, one "
+                                          f"transmitter per process, to residual {args.tol:g}; {len(walls)} rounds"}
+    print(json.dumps(line), flush=True)
+    net.close()
+    ctx.close()
+
+
+def _c4_worker(t, tol, rounds, barrier, queue):
+    from oracle import grad, model
+    from paper_1708_01663_gb300 import train_fno
+    ang, rx = train_fno.geometry()
+    prob = model.Problem(train_fno.N, train_fno.DELTA, np.asarray(ang)[[t]], rx)
+    f = train_fno.phantom(100000).astype(np.complex128)
+    for _ in range(rounds):
+        barrier.wait()
+        t0 = time.perf_counter()
+        grad.forward(prob, f, tol)
+        queue.put((t0, time.perf_counter()))
+
+
+def _oracle_rounds_c4(tol, rounds=3):
+    import multiprocessing as mp
+    from paper_1708_01663_gb300 import train_fno
+    workers = max(1, min(os.cpu_count() or 1, train_fno.T))
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(workers), ctx.Queue()
+    procs = [ctx.Process(target=_c4_worker, args=(w, tol, rounds, barrier, queue)) for w in range(workers)]
+    for p in procs:
+        p.start()
+    walls = []
+    for _ in range(rounds):
+        marks = [queue.get(timeout=3600) for _ in range(workers)]
+        walls.append(max(m[1] for m in marks) - min(m[0] for m in marks))
+    for p in procs:
+        p.join()
+    return walls, workers
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "c4":
+        run_c4(args)
         return
     ws, rank, local = _dist()
     import torch
@@ -302,37 +569,50 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1708_01663_gb300 import build, cisor, synth
+    from paper_1708_01663_gb300 import build, cisor, shard, synth
     build.build()
     dev = torch.device("cuda", local)
     cfg, f_true, angles, rx = synth.make_inputs(args.config)
     n, T, M, dim = cfg["n"], cfg["T"], cfg["M"], cfg["dim"]
     complex_f = cfg["imag"] != 0.0
     vec = bool(cfg.get("vectorial"))
+    # N > 1: weak scaling by transmitter shards.  One reconstruction with N x T plane waves at uniform
+    # angles; rank r solves its contiguous block of T and the ranks all-reduce g and D once per step.
+    sharded = ws > 1 and dim == 2 and cfg.get("tx_kind", 0) in (0, "plane") and not vec
+    T_total = T * ws if sharded else T
+    if sharded:
+        angles = synth.plane_wave_angles(T_total)[rank * T:(rank + 1) * T]
     ctx = cisor.Cisor(n, cfg["delta"], angles, rx, complex_f=complex_f, dim=dim, tx_kind=cfg.get("tx_kind", 0),
                       vectorial=vec)
     if "rx_mask" in cfg:
         ctx.set_rx_mask(cfg["rx_mask"])
     if args.cols_cta:
         ctx.set_cols_cta(args.cols_cta)
-        cols_nt = args.cols_cta
+        ctx.set_tx_chunk(max(args.tx_chunk, 0))
     else:
-        cols_nt = ctx.autotune(reps=10)  # pick the column-kernel shape by measurement
+        ctx.autotune(reps=10)  # pick the column-kernel shape and transmitter chunk by measurement
+        if args.tx_chunk >= 0:
+            ctx.set_tx_chunk(args.tx_chunk)
+    cols_nt, tx_chunk = ctx.tuning()
 
     # synthetic measurements: GPU forward model of the phantom + seeded 40 dB noise (untimed set-up)
     f_dev = torch.from_numpy(np.ascontiguousarray(f_true, dtype=np.complex64)).to(dev)
     y_dev = torch.empty((T, M), dtype=torch.complex64, device=dev)
     ctx.forward(f_dev, y_out=y_dev, tol=1e-6, max_iter=args.max_iter, check=False)
     torch.cuda.synchronize()
-    noise = torch.from_numpy(synth.complex_noise(cfg["seed"] + 100, (T, M)).astype(np.complex64)).to(dev)
-    sigma = float(torch.linalg.vector_norm(y_dev)) * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(T * M)
+    noise = synth.complex_noise(cfg["seed"] + 100, (T_total, M)).astype(np.complex64)
+    noise = torch.from_numpy(noise[rank * T:(rank + 1) * T] if sharded else noise).to(dev)
+    ny2 = torch.tensor([float(torch.linalg.vector_norm(y_dev)) ** 2], dtype=torch.float64, device=dev)
+    if sharded:
+        dist.all_reduce(ny2)
+    sigma = float(ny2.item()) ** 0.5 * 10 ** (-cfg["snr_db"] / 20) / np.sqrt(T_total * M)
     y_dev += sigma * noise
     H_dev = torch.empty((M, ctx.Nf), dtype=torch.complex64, device=dev)
     ctx.sensing_matrix(H_dev)
     u_in = torch.empty((T, ctx.Nf), dtype=torch.complex64, device=dev)
     ctx.incident(u_in)
     # L_Born <= T max|u_in|^2 ||H||_F^2 (max |u_in| = 1 for plane waves)
-    gamma = 1.0 / (T * float(u_in.abs().max()) ** 2 * float(torch.linalg.vector_norm(H_dev)) ** 2)
+    gamma = 1.0 / (T_total * float(u_in.abs().max()) ** 2 * float(torch.linalg.vector_norm(H_dev)) ** 2)
     del H_dev, u_in
 
     s0 = torch.from_numpy(_state0(f_true)).to(dev)
@@ -343,11 +623,17 @@ def main():
     infos = []
     iters_all = []
 
+    g_red = torch.empty_like(s0)  # the all-reduced gradient of a sharded step
+
     def step(st, y, f_buf, s_buf):
         f_buf.copy_(s0) if hasattr(f_buf, "copy_") else None
         s_buf.copy_(s0) if hasattr(s_buf, "copy_") else None
         st.t, st.k = 1.0, 1
-        _, info = ctx.step(st, y, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
+        if sharded:  # this rank's gradient, NCCL all-reduce of g and D, redundant update (Eqs. 9-11)
+            _, info = shard.sharded_step(ctx, st, s_buf, y, g_red, tol=args.tol, max_iter=args.max_iter, x0_mode=0,
+                                         check=False)
+        else:
+            _, info = ctx.step(st, y, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
         infos.append(info.as_dict())
         iters_all.extend(ctx.solve_iterations(False).tolist() + ctx.solve_iterations(True).tolist())
 
@@ -409,7 +695,11 @@ def main():
         f_h.copy_(s0_h)
         s_h.copy_(s0_h)
         st_h.t, st_h.k = 1.0, 1
-        ctx.step(st_h, y_h, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
+        if sharded:
+            shard.sharded_step(ctx, st_h, s_h, y_h, g_red, tol=args.tol, max_iter=args.max_iter, x0_mode=0,
+                               check=False)
+        else:
+            ctx.step(st_h, y_h, tol=args.tol, max_iter=args.max_iter, x0_mode=0, check=False)
 
     step_h()
     torch.cuda.synchronize()
@@ -439,7 +729,7 @@ def main():
     achieved_tf = alg_flops / (mv_ms * 1e-3) / 1e12
     achieved_gbs = alg_bytes / (mv_ms * 1e-3) / 1e9
     hbm_peak, peak_kind = _peaks()
-    fp32_peak = FP32_PEAK_TFLOPS
+    fp32_peak, peak_inputs = _fp32_peak(local)
     traffic = _traffic_summary(args.config)
     fshape = (T, 3) + (n,) * dim if vec else (T,) + (n,) * dim
     u_in = torch.empty(fshape, dtype=torch.complex64, device=dev)
@@ -451,12 +741,10 @@ def main():
     field_err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         s0n = _state0(f_true).astype(np.complex128)
-        txs = [0, 1]
-        nsolve, sec, note, _ = _oracle_sample_solves(cfg, s0n, angles, rx, txs, args.tol)
-        if sec < 5.0:  # small workloads: enough transmitters for about 5 s of oracle work
-            txs = [t % T for t in range(min(64, max(2, int(2 * 5.0 / max(sec, 1e-3)))))]
-            nsolve, sec, note, _ = _oracle_sample_solves(cfg, s0n, angles, rx, txs, args.tol)
-        cpu = {"value": nsolve / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note}
+        walls, workers = _oracle_rounds(args.config, T, args.tol, 2)
+        note = _oracle_sample_note(args.config, cfg, workers, args.tol) + f"; {len(walls)} rounds"
+        cpu = {"value": 2 * workers * len(walls) / sum(walls), "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": note}
         # error of the converged field (GPU, residual tol) against a tight FP64 oracle solve of transmitter 0
         _, _, _, ref = _oracle_sample_solves(cfg, s0n, angles, rx, [0], 1e-9)
         u_dev = torch.empty((T, 3) + (n,) * dim if vec else (T,) + (n,) * dim, dtype=torch.complex64, device=dev)
@@ -473,14 +761,19 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": _workload(args.config, cfg),
+            "config": {"workload": _workload(args.config, dict(cfg, T=T_total)) + (
+                           f" ({T} per rank)" if sharded else ""),
                        "step": "one relaxed-FISTA iteration from a fixed state: T forward + T adjoint "
                                "cold-start solves to residual 1e-4, sensing, gradient, FGP prox (20 it)",
                        "solves_per_step": solves_per_step, "start": "cold (u_in / 0)",
                        "l2": (f"working set > L2 (Krylov vectors 12 x {T * N * 8 / 2**20:.0f} MB)" if flush is None
                               else "L2 flushed between timed steps (512 MB write outside the timed windows)"),
-                       "parallelism": "independent replicas" if ws > 1 else "single GPU",
+                       "parallelism": (f"transmitter shards: {ws} ranks x {T} of {T_total} plane waves, NCCL "
+                                       "all-reduce of g and D per step, redundant prox and momentum") if sharded
+                                      else ("independent replicas" if ws > 1 else "single GPU"),
                        "cols_cta": cols_nt, "cols_cta_from": "flag" if args.cols_cta else "autotune",
+                       "tx_chunk": tx_chunk,
+                       "tx_chunk_from": "flag" if (args.cols_cta or args.tx_chunk >= 0) else "autotune",
                        "fwd_iters_mean": float(np.mean(it_f)) if it_f else None,
                        "fwd_iters_max": max(i["iters_max"] for i in step_infos) if step_infos else None,
                        "adj_iters_max": max(i["adj_iters_max"] for i in step_infos) if step_infos else None,
@@ -497,9 +790,17 @@ def main():
                                    + (" per field component, + the grad-div stencil)" if vec else ")"),
                          "ms_per_launch": mv_ms, "alg_flops_per_launch": alg_flops,
                          "alg_bytes_per_launch": alg_bytes,
-                         "peak_kind": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                         "peak_kind": "FP32 FMA peak from the device's attributes: SMs x FP32 lanes per SM x 2 "
+                                      "flops x peak SM clock",
+                         "peak_inputs": peak_inputs,
                          "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                 "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth"}},
+                                 "frac": achieved_gbs / hbm_peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                                 "what": "algorithmic bytes (read x, write A x per transmitter, f once) / CUDA-event "
+                                         "time of one pass",
+                                 "dram_achieved": (traffic / (mv_ms * 1e-3) / 1e9) if traffic else None,
+                                 "dram_frac": (traffic / (mv_ms * 1e-3) / 1e9 / hbm_peak) if traffic else None,
+                                 "dram_what": "ncu DRAM bytes of one pass (profiles/, cold cache) / CUDA-event time "
+                                              "of one pass; null when the kernels changed since the capture"}},
             "comparison": {"cufft_matvec_ms": cufft_ms, "cisor_matvec_ms": mv_ms,
                            "what": "the same batched A x over all T with torch.fft (cuFFT: pad, FFT, x ghat, IFFT, "
                                    "crop) on the same inputs; timed for comparison only, not on the product path"},

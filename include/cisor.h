@@ -246,7 +246,8 @@ cisor_status cisor_time_matvec(cisor_ctx* ctx, const void* f, int adjoint, int r
 cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const void* x, void* y, int n, int P,
                                   int nvec, int adjoint, void* stream);
 
-/* Autotuner of the FFT convolution's column-kernel shape: times the
+/* Autotuner of the FFT convolution's column-kernel shape and transmitter
+ * chunk (cisor_set_tx_chunk): times the
  * three-stage (8 x 8 x 8 at P = 512) column kernel with 512- and 256-thread
  * CTAs (8 or 4 columns per CTA at P = 512) and, where it exists, the
  * two-stage kernel (shape code 16: one shared-memory exchange per transform;
@@ -256,6 +257,30 @@ cisor_status cisor_apply_A_static(const void* ghat_scaled, const void* f, const 
  * receives the chosen shape code (512, 256 or 16).  Results agree to FP32
  * rounding whichever shape runs. */
 cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
+
+/* Split every FFT-convolution pass into consecutive launches of `tx_chunk`
+ * transforms (transmitters; field components in the vectorial model), each
+ * running the whole row / column / row chain before the next; 0 = all at
+ * once.  The chunks share the start of the row-FFT intermediate, so a chunk
+ * small enough for L2 keeps it there instead of writing it to HBM and reading
+ * it back.  cisor_autotune measures chunks of about 16, 32 and 48 MB of
+ * intermediate against no chunking and keeps the fastest (with the column
+ * shape).  Results are identical whatever the chunk. */
+cisor_status cisor_set_tx_chunk(cisor_ctx* ctx, int tx_chunk);
+
+/* How a solve's BiCGSTAB iterations are driven.  device_loop = 1 (the
+ * default): the whole solve is ONE CUDA-graph launch whose WHILE node repeats
+ * a captured chunk of iterations until no transmitter is active (a device-side
+ * condition kernel decides; the loop count is capped at max_iter / chunk + 2),
+ * so the host waits once per solve.  device_loop = 0: the host replays a
+ * chunk graph and reads the active flags after every chunk.  Results are
+ * identical; where conditional graph nodes are unavailable the library falls
+ * back to 0 by itself. */
+cisor_status cisor_set_solve_loop(cisor_ctx* ctx, int device_loop);
+
+/* The context's current column shape (512, 256 or 16) and transmitter chunk
+ * (0 = none); either output may be NULL. */
+cisor_status cisor_tuning(const cisor_ctx* ctx, int* cols_nt, int* tx_chunk);
 
 /* Per-transmitter receiver mask (the Fresnel set-ups of Sec. IV record each
  * transmitter on a subset of the receivers): mask [T, M] bytes, non-zero =
@@ -289,6 +314,12 @@ typedef struct cisor_batch cisor_batch;
  * cisor_autotune on each. */
 cisor_status cisor_batch_create(cisor_batch** out, const cisor_geometry* geoms, int nprob, void* stream,
                                 int autotune);
+/* As cisor_set_solve_loop for a batch: device_loop = 1 (default) runs each
+ * solve of all problems as one graph launch with a device-side loop over
+ * chunks of iterations of every problem; 0 replays a chunk graph per host
+ * iteration. */
+cisor_status cisor_batch_set_solve_loop(cisor_batch* batch, int device_loop);
+
 cisor_status cisor_batch_destroy(cisor_batch* b);
 
 /* The context of problem i (for table read-back or single-problem calls). */

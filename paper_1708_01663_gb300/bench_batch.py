@@ -7,9 +7,10 @@ sides 256, 256, 512, 512), 32 / 64 / 96 / 128 plane-wave transmitters
 (assigned to the grids by a seeded shuffle), 128 receivers on a circle at 1.5
 half-widths, seeded random ellipses with contrast in [0, 0.8] plus 0.02i.
 Cold-start forward solves to relative residual 1e-4.  Prints one JSON line:
-LS field solves per second for the batch (one CUDA-graph launch per chunk of
-iterations advancing every problem) and for the same contexts solved
-sequentially, both timed with CUDA events on the caller's stream.
+LS field solves per second for the batch (one CUDA-graph launch per solve: a
+device-side WHILE loop over chunks of iterations advancing every problem) and
+for the same contexts solved sequentially, both timed with CUDA events on the
+caller's stream; and both again with the host-driven chunk loop.
 """
 from __future__ import annotations
 
@@ -75,11 +76,23 @@ def main():
 
     ms_batch = timed(run_batch)
     ms_seq = timed(run_seq)
+    batch.set_solve_loop(False)  # the host-driven chunk loop, for comparison
+    for p in batch.problems:
+        p.set_solve_loop(False)
+    ms_batch_host = timed(run_batch)
+    ms_seq_host = timed(run_seq)
+    batch.set_solve_loop(True)
+    for p in batch.problems:
+        p.set_solve_loop(True)
     print(json.dumps({
         "workload": "grids 96/128/192/256, 32-128 Tx each, 128 Rx, contrast<=0.8+0.02i, cold start to 1e-4",
         "solves": solves, "batch_ms": ms_batch, "sequential_ms": ms_seq,
         "batch_solves_per_s": solves / (ms_batch / 1e3), "sequential_solves_per_s": solves / (ms_seq / 1e3),
         "speedup": ms_seq / ms_batch,
+        "host_loop": {"batch_ms": ms_batch_host, "sequential_ms": ms_seq_host,
+                      "what": "the same solves with the host replaying a 4-iteration chunk graph and reading the "
+                              "active flags after every chunk"},
+        "tuning": [p.tuning() for p in batch.problems],
         "P": [p.P for p in batch.problems], "T": [p.T for p in batch.problems],
         "iters_max": [i["iters_max"] for i in infos["batch"]],
         "iters_mean": [round(i["iters_mean"], 1) for i in infos["batch"]],

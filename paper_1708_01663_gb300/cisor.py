@@ -100,6 +100,10 @@ def load(path: str = LIB_PATH):
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
         "cisor_data_term": [vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
         "cisor_autotune": [vp, i, POINTER(c_int)],
+        "cisor_set_tx_chunk": [vp, c_int],
+        "cisor_tuning": [vp, POINTER(c_int), POINTER(c_int)],
+        "cisor_set_solve_loop": [vp, c_int],
+        "cisor_batch_set_solve_loop": [vp, c_int],
         "cisor_fno_create": [POINTER(c_void_p), i, ctypes.c_ulonglong, vp],
         "cisor_fno_destroy": [vp],
         "cisor_fno_num_params": [vp, POINTER(c_longlong)],
@@ -246,6 +250,20 @@ class Cisor:
         assert m.shape == (self.T, self.M)
         self._mask = m
         return _check(self._lib.cisor_set_rx_mask(self._ctx, m.ctypes.data_as(c_void_p)))
+
+    def set_tx_chunk(self, chunk):
+        """Transforms per FFT-convolution launch (0: all at once); results do not depend on it."""
+        return _check(self._lib.cisor_set_tx_chunk(self._ctx, int(chunk)))
+
+    def set_solve_loop(self, device_loop=True):
+        """1: whole solve in one graph launch (device-side loop); 0: host-driven chunks."""
+        return _check(self._lib.cisor_set_solve_loop(self._ctx, 1 if device_loop else 0))
+
+    def tuning(self):
+        """(column shape, transmitter chunk) in use."""
+        a, b = c_int(), c_int()
+        _check(self._lib.cisor_tuning(self._ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def set_cols_cta(self, nt):
         """Column-kernel shape: 512 or 256 threads of the three-stage kernel, or 16 (two-stage; P = 128, 256, 2D 512)."""
@@ -414,6 +432,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_solve_loop(self, device_loop=True):
+        """1: each solve of all problems in one graph launch (device-side loop); 0: host-driven chunks."""
+        return _check(self._lib.cisor_batch_set_solve_loop(self._b, 1 if device_loop else 0))
 
     def _ptrs(self, arrs, counts):
         return (c_void_p * len(arrs))(*[ptr(a, c) if a is not None else None for a, c in zip(arrs, counts)])

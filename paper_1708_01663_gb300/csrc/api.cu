@@ -167,11 +167,27 @@ static cisor_status grad_core(cisor_ctx* c, const cisor_solve_opts* o, double ga
   return worse(s1, s2);
 }
 
+// Captured graphs hold the kernel variants and launch sequence they were built with.
+static cisor_status drop_graphs(cisor_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->graph[i]) CISOR_CUDA(cudaGraphExecDestroy(c->graph[i]));
+    if (c->wgraph[i]) CISOR_CUDA(cudaGraphExecDestroy(c->wgraph[i]));
+    c->graph[i] = nullptr;
+    c->wgraph[i] = nullptr;
+  }
+  return CISOR_OK;
+}
+
 static void free_ctx(cisor_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 2; ++i) {
     if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    if (c->wgraph[i]) cudaGraphExecDestroy(c->wgraph[i]);
+  }
+  if (c->loop_item) cudaFree(c->loop_item);
+  if (c->loop_count) cudaFree(c->loop_count);
+  if (c->h_loop_count) cudaFreeHost(c->h_loop_count);
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
@@ -278,6 +294,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->rx_pos.assign(g->rx_pos, g->rx_pos + (size_t)d * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
+  c->use_while = 1;
   c->cols_nt = 512;
   conv_geometry(c);
   {
@@ -734,12 +751,39 @@ cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
   }
   if (cols_nt != c->cols_nt) {
     c->cols_nt = cols_nt;
-    for (int i = 0; i < 2; ++i)  // captured graphs hold the previous kernel variant
-      if (c->graph[i]) {
-        CISOR_CUDA(cudaGraphExecDestroy(c->graph[i]));
-        c->graph[i] = nullptr;
-      }
+    CISOR_TRY(drop_graphs(c));
   }
+  return CISOR_OK;
+}
+
+cisor_status cisor_set_tx_chunk(cisor_ctx* c, int tx_chunk) {
+  if (!c || tx_chunk < 0) {
+    set_error("cisor_set_tx_chunk: NULL context or negative chunk");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (tx_chunk != c->tx_chunk) {
+    c->tx_chunk = tx_chunk;
+    CISOR_TRY(drop_graphs(c));
+  }
+  return CISOR_OK;
+}
+
+cisor_status cisor_set_solve_loop(cisor_ctx* c, int device_loop) {
+  if (!c || (device_loop != 0 && device_loop != 1)) {
+    set_error("cisor_set_solve_loop: NULL context or mode not 0 / 1");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  c->use_while = device_loop;
+  return drop_graphs(c);
+}
+
+cisor_status cisor_tuning(const cisor_ctx* c, int* cols_nt, int* tx_chunk) {
+  if (!c) {
+    set_error("cisor_tuning: NULL context");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (cols_nt) *cols_nt = c->cols_nt;
+  if (tx_chunk) *tx_chunk = c->tx_chunk;
   return CISOR_OK;
 }
 
@@ -769,32 +813,41 @@ cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   CISOR_CUDA(cudaEventCreate(&e1));
   const int variants[3] = {512, 256, COLS_TWO_STAGE};
   const int nvar = two_stage_ok(c) ? 3 : 2;
-  int best = 512;
+  // transmitter chunks whose FFT intermediate takes about 16, 32 or 48 MB (L2 is 126 MB), and no chunking
+  const int ntr = c->T * c->ncomp;
+  const long long rbytes = (long long)c->rtstride * (long long)sizeof(float2);
+  int chunks[4] = {0, 0, 0, 0};
+  int nch = 1;
+  for (int mb = 16; mb <= 48; mb += 16) {
+    const long long k = ((long long)mb << 20) / rbytes;
+    if (k >= 1 && k < ntr && (nch == 1 || k != chunks[nch - 1])) chunks[nch++] = (int)k;
+  }
+  int best = 512, best_chunk = 0;
   float best_ms = 1e30f;
   cisor_status st = CISOR_OK;
-  for (int v = 0; v < nvar && st == CISOR_OK; ++v) {
-    c->cols_nt = variants[v];
-    st = matvec_once(c, 0, c->T, c->s, c->tv);  // warm-up
-    CISOR_CUDA(cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < reps && st == CISOR_OK; ++i) st = matvec_once(c, 0, c->T, c->s, c->tv);
-    CISOR_CUDA(cudaEventRecord(e1, c->stream));
-    CISOR_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CISOR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = variants[v];
+  for (int v = 0; v < nvar && st == CISOR_OK; ++v)
+    for (int h = 0; h < nch && st == CISOR_OK; ++h) {
+      c->cols_nt = variants[v];
+      c->tx_chunk = chunks[h];
+      st = matvec_once(c, 0, c->T, c->s, c->tv);  // warm-up
+      CISOR_CUDA(cudaEventRecord(e0, c->stream));
+      for (int i = 0; i < reps && st == CISOR_OK; ++i) st = matvec_once(c, 0, c->T, c->s, c->tv);
+      CISOR_CUDA(cudaEventRecord(e1, c->stream));
+      CISOR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CISOR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = variants[v];
+        best_chunk = chunks[h];
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CISOR_TRY(st);
   c->cols_nt = best;
-  for (int i = 0; i < 2; ++i)  // captured graphs hold the previous kernel variant
-    if (c->graph[i]) {
-      cudaGraphExecDestroy(c->graph[i]);
-      c->graph[i] = nullptr;
-    }
+  c->tx_chunk = best_chunk;
+  CISOR_TRY(drop_graphs(c));
   if (cols_nt_out) *cols_nt_out = best;
   return call.leave();
 }

@@ -26,8 +26,13 @@ namespace {
 void free_batch(cisor_batch* b) {
   if (!b) return;
   if (b->ms.main) cudaStreamSynchronize(b->ms.main);
-  for (int d = 0; d < 2; ++d)
+  for (int d = 0; d < 2; ++d) {
     if (b->ms.graph[d]) cudaGraphExecDestroy(b->ms.graph[d]);
+    if (b->ms.wgraph[d]) cudaGraphExecDestroy(b->ms.wgraph[d]);
+  }
+  if (b->ms.items) cudaFree(b->ms.items);
+  if (b->ms.loop_count) cudaFree(b->ms.loop_count);
+  if (b->ms.h_loop_count) cudaFreeHost(b->ms.h_loop_count);
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
   if (b->ms.fork) cudaEventDestroy(b->ms.fork);
@@ -133,6 +138,10 @@ cisor_status cisor_batch_create(cisor_batch** out, const cisor_geometry* geoms, 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   b->join.assign(nprob, nullptr);
   for (int i = 0; i < nprob && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->ms.items, sizeof(cisor_loop_item) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->ms.loop_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->ms.h_loop_count, sizeof(int));
+  b->ms.use_while = 1;
   if (e != cudaSuccess) {
     cisor_status st = cuda_fail(e, "batch stream/event setup", __FILE__, __LINE__);
     free_batch(b);
@@ -144,6 +153,20 @@ cisor_status cisor_batch_create(cisor_batch** out, const cisor_geometry* geoms, 
     b->ms.kernels[d] = b->kern[d].data();
   }
   *out = b;
+  return CISOR_OK;
+}
+
+cisor_status cisor_batch_set_solve_loop(cisor_batch* b, int device_loop) {
+  if (!b || (device_loop != 0 && device_loop != 1)) {
+    set_error("cisor_batch_set_solve_loop: NULL batch or mode not 0 / 1");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (b->ms.main) CISOR_CUDA(cudaStreamSynchronize(b->ms.main));
+  for (int d = 0; d < 2; ++d) {
+    if (b->ms.wgraph[d]) CISOR_CUDA(cudaGraphExecDestroy(b->ms.wgraph[d]));
+    b->ms.wgraph[d] = nullptr;
+  }
+  b->ms.use_while = device_loop;
   return CISOR_OK;
 }
 

@@ -130,7 +130,15 @@ struct cisor_ctx {
   float *tv_z, *tv_r0, *tv_r1, *tv_p;
   float *tva0, *tva1;  // anisotropic TV: (2d + 1) auxiliary images per plane, ping-pong
   float2* vbuf;        // vectorial model: conv output / grad-div pre-pass [T, 3, N]
-  // graphs of a chunk of BiCGSTAB iterations
+  // whole-solve graphs: a device-side WHILE loop over chunks of BiCGSTAB iterations
+  cudaGraphExec_t wgraph[2];
+  int wgraph_ntx[2];
+  float2* wgraph_x[2];
+  int* loop_count;            // device: loop-body executions of the current launch
+  int* h_loop_count;          // pinned copy
+  struct cisor_loop_item* loop_item;  // device [1]: this context's active flags for the loop condition
+  int use_while;              // 1 until building a WHILE graph fails (then the host-driven chunk loop)
+  // graphs of a chunk of BiCGSTAB iterations (host-driven loop)
   cudaGraphExec_t graph[2];
   int graph_ntx[2];
   float2* graph_x[2];
@@ -139,8 +147,17 @@ struct cisor_ctx {
   long long launches;       // kernels launched (graph replays add their kernel count)
   int cols_nt;              // column-FFT kernel shape (512 or 256 threads of the three-stage kernel, or
                             // COLS_TWO_STAGE), set by the autotuner
+  int tx_chunk;             // transforms per convolution launch (0: all at once); every chunk reuses the
+                            // start of R, so a chunk's intermediate can stay in L2 between its kernels
   long long graph_kernels[2];
   std::vector<int> last_iters[2];  // per-transmitter iterations of the last forward / adjoint solve
+};
+
+// One problem's per-transmitter active flags, read by the device-side loop
+// condition of a whole-solve graph.
+struct cisor_loop_item {
+  const int* active;
+  int ntx;
 };
 
 namespace cisor {
@@ -187,6 +204,8 @@ struct ConvOp {
   int ntx;
   int tx_div;             // transforms per transmitter (3: the field components of the vectorial
                           // model run as consecutive transforms; 0 or 1: one)
+  int tx0;                // first transform of this launch (set by conv_pass when it splits a pass
+                          // into transmitter chunks; R is indexed from the chunk's start)
 };
 enum { PRO_COPY = 0, PRO_PUPDATE = 1, PRO_AXPY = 2 };
 // Programmatic dependent launch (sm_90 and later): the solver chain's kernels
@@ -248,8 +267,13 @@ struct MultiSolve {
   cudaStream_t main;
   cudaEvent_t fork;
   cudaEvent_t* join;            // [np]
-  cudaGraphExec_t graph[2];     // forward / adjoint chunk graphs
+  cudaGraphExec_t graph[2];     // forward / adjoint chunk graphs (host-driven loop)
+  cudaGraphExec_t wgraph[2];    // forward / adjoint whole-solve graphs (device-side WHILE loop)
   long long* kernels[2];        // [np] kernels per problem in one replay
+  struct cisor_loop_item* items;  // device [np]: every problem's active flags
+  int* loop_count;              // device
+  int* h_loop_count;            // pinned
+  int use_while;
 };
 cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2* const* b, double tol, int max_iter,
                          MultiSolve& ms, SolveStat* st);

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
   __shared__ float2 buf[C::RB * C::PP];
   pdl_trigger();
   pdl_wait();
-  const int tx = blockIdx.y;
+  const int tx = op.tx0 + blockIdx.y;                    // transform (vectors, scalars, flags)
   const int txs = op.tx_div > 1 ? tx / op.tx_div : tx;  // transmitter of this transform
   if (op.active && !op.active[txs]) return;
   const int n = geo.n;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) conv_rows_fwd(const ConvOp op, const floa
                                  RowSync<P>{row});
   if (!rowok) return;
   constexpr int RL = PL::template last<false>();
-  float2* dst = R + r_row<P>(geo, tx, iy);
+  float2* dst = R + r_row<P>(geo, blockIdx.y, iy);  // R holds the chunk's transforms from its start
 #pragma unroll
   for (int q = 0; q < 8 / RL; ++q)
 #pragma unroll
@@ -144,6 +144,7 @@ struct ColGeo {
   int n, cps;  // column blocks per slab (P / W)
   long long es, slab, tstride;
   int tx_div;
+  int tx0;     // first transform of the launch (R starts at the chunk's first transform)
 };
 
 // Dynamic shared memory of the column kernel, in float2: the exchange
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
   float2* twr = tw + SM::TW;
   pdl_trigger();
   pdl_wait();
-  const int tx = blockIdx.y;
+  const int tx = geo.tx0 + blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
   const int w = threadIdx.x % W, lt = threadIdx.x / W;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) conv_cols(const int* __restrict
     for (int i = threadIdx.x; i < TwTable<P, false>::SIZE; i += NT) tw[i] = tw_g[i];
   if (MODE != COL_FWD)
     for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += NT) twr[i] = tw_g[TW_STRIDE + i];
-  float2* base = R + tx * geo.tstride + j * geo.slab + c0 + w;
+  float2* base = R + blockIdx.y * geo.tstride + j * geo.slab + c0 + w;
   const ColLay<W> lay{w};
   const ColLayRev<P, W> layr{w};
   float2 v[8];
@@ -289,14 +290,14 @@ __global__ void __launch_bounds__(256, TwoStage<P>::MINB)
   extern __shared__ __align__(16) float2 smem[];  // [P rows][W columns], then P twiddles
   pdl_trigger();
   pdl_wait();
-  const int tx = blockIdx.y;
+  const int tx = geo.tx0 + blockIdx.y;
   if (active && !active[geo.tx_div > 1 ? tx / geo.tx_div : tx]) return;
   const int n = geo.n;
   const int w = threadIdx.x % W, lt = threadIdx.x / W;
   const int j3 = D3 ? blockIdx.x / geo.cps : 0;
   const int c0 = (D3 ? blockIdx.x % geo.cps : blockIdx.x) * W;
   const long long es = D3 ? geo.es : P;
-  float2* base = R + tx * geo.tstride + j3 * geo.slab + c0 + w;
+  float2* base = R + blockIdx.y * geo.tstride + j3 * geo.slab + c0 + w;
   // the twiddle table in shared memory (first read after a barrier); read from
   // global memory it cost 6 % more time at P = 512
   float2* tws = smem + P * W;
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   __shared__ float2 buf[C::RB * C::PP];
   pdl_trigger();
   pdl_wait();
-  const int tx = blockIdx.y;
+  const int tx = op.tx0 + blockIdx.y;
   if (op.active && !op.active[op.tx_div > 1 ? tx / op.tx_div : tx]) return;
   const int n = geo.n;
   const int lt = threadIdx.x % C::NTF, row = threadIdx.x / C::NTF;
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const floa
   for (int i = threadIdx.x; i < TwTable<P, true>::SIZE; i += 256) tw[i] = tw_g[TW_STRIDE + i];
   if (P / 8 < 32) __syncthreads();  // the twiddle table is shared by rows that sync per warp
   constexpr int R0 = PL::template first<true>();
-  const float2* srow = R + r_row<P>(geo, tx, rowok ? iy : 0);
+  const float2* srow = R + r_row<P>(geo, blockIdx.y, rowok ? iy : 0);
   float2 v[8];
 #pragma unroll
   for (int q = 0; q < 8 / R0; ++q)
@@ -493,7 +494,7 @@ template <int P, int MODE, bool ADJ, int NT>
 static void launch_cols(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
   constexpr int W = ConvCfg<P>::template Col<NT>::W;
   constexpr size_t SMB = ColSmem<P, MODE, NT>::BYTES;
-  const ColGeo geo{c->n, P / W, es, slab, c->rtstride, op.tx_div};
+  const ColGeo geo{c->n, P / W, es, slab, c->rtstride, op.tx_div, op.tx0};
   dim3 g((P / W) * nslab, op.ntx);
   if constexpr (P <= 256) {  // 3D grids use P <= 256
     if (c->dim == 3) {
@@ -554,7 +555,7 @@ template <int P, int MODE, bool ADJ>
 static void launch_cols_2s(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
   if constexpr (P >= 128) {
     typedef TwoStage<P> TS;
-    const ColGeo geo{c->n, P / TS::W, es, slab, c->rtstride, op.tx_div};
+    const ColGeo geo{c->n, P / TS::W, es, slab, c->rtstride, op.tx_div, op.tx0};
     const dim3 g((P / TS::W) * nslab, op.ntx);
     if constexpr (P <= 256) {
       if (c->dim == 3) {
@@ -592,7 +593,7 @@ static void cols_pass(cisor_ctx* c, const ConvOp& op, int nslab, long long es, l
 }
 
 template <int P>
-static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
+static cisor_status conv_chunk_t(cisor_ctx* c, const ConvOp& op) {
   typedef ConvCfg<P> C;
   const int n = c->n;
   const RowGeo rg{n, c->nrows, c->rslab, c->rtstride};
@@ -638,6 +639,23 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
 #undef CISOR_ROWS_INV
   CISOR_CUDA(cudaGetLastError());
   c->launches += conv_kernels_per_pass(c->dim);
+  return CISOR_OK;
+}
+
+// One pass over op.ntx transforms, as consecutive chunks of c->tx_chunk
+// transforms (all at once when 0): each chunk runs the whole row / column /
+// row chain before the next starts and they all use the start of R, so with
+// a chunk's intermediate sized below L2 it is written and read back there
+// instead of round-tripping through HBM.
+template <int P>
+static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
+  const int chunk = (c->tx_chunk > 0 && c->tx_chunk < op.ntx) ? c->tx_chunk : op.ntx;
+  for (int t0 = 0; t0 < op.ntx; t0 += chunk) {
+    ConvOp o = op;
+    o.tx0 = op.tx0 + t0;
+    o.ntx = op.ntx - t0 < chunk ? op.ntx - t0 : chunk;
+    CISOR_TRY(conv_chunk_t<P>(c, o));
+  }
   return CISOR_OK;
 }
 

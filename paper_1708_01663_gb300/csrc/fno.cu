@@ -9,24 +9,44 @@
 //        unit local propagation direction of u_in (phase gradient by central
 //        differences, clamped at the edges)
 //   v0 = W0 a + b0                                       1x1 lifting
-//   v_l = GELU(Lsyn(R_l . S(v_{l-1})) + W_l v_{l-1} + b_l)  (no GELU on the last)
+//   v_{l+1} = GELU(Lsyn(R_l . S(v_l)) + W_l v_l + b_l)   (no GELU on the last)
 //   out = P2 GELU(P1 v_4 + c1) + c2,  e = out_0 + j out_1, predicted u - u_in = u_in e
-// (the demodulated target keeps forward-scattered energy at low frequencies,
-// inside the 16 retained modes; the incident carrier itself sits at 16 cycles
-// per side at lambda/8)
-// S keeps kx in {0..15, 112..127} (rows) x ky in {0..15} (columns) of the
-// 2D DFT; Lsyn is (1/128^2) Re of the truncated inverse with weight 2 on
-// ky > 0.  Loss: mean over samples of ||out - t|| / ||t||.
-// Weights are held in FP32 (master, Adam state) and read by the kernels from
-// a BF16 copy; activations and accumulation are FP32.  The 2D transforms use
-// the register-boundary Stockham FFT (P = 128) with pruned inputs/outputs.
+// S keeps kx in {0..15, 112..127} (rows) x ky in {0..15} (columns) of the 2D
+// DFT; Lsyn is (1/128^2) Re of the truncated inverse with weight 2 on ky > 0.
+// Loss: mean over samples of ||out - t|| / ||t||.
+//
+// Every contraction runs on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation): the truncated DFTs are small dense GEMMs
+// against FP64-built cosine/sine tables (16 of 128 frequencies per axis, so a
+// GEMM reads each value once where a full FFT would transform 8x more), the
+// 1x1 channel mixings, the projection, and the weight gradients (reductions
+// over pixels or samples).  Weights are BF16 (the model is defined by their
+// BF16 values; FP32 master copies and Adam state), so a weight operand is
+// exact; activations and tables are split into BF16 hi + lo parts and a
+// product takes two or three MMAs (about 16 mantissa bits, the accuracy of
+// FP32 arithmetic for these sums).  Only the per-mode 32 x 32 mixing of the
+// forward pass and its transpose in the backward pass (vector x matrix per
+// sample and mode) run on the FP32 pipes.
+//
+// A layer is two kernels:
+//   row kernel     (one sample, 2 image rows, all 32 channels): inverse row
+//                  DFT of the mode-mixed spectrum + W v + b, GELU, and the
+//                  forward row DFT of the result for the next layer (or the
+//                  projection after the last layer);
+//   column kernel  (one sample, one ky): column DFT to the 32 kept kx, mode
+//                  mixing with R_l, inverse column DFT.
+// Between them the spectra travel as [B][64 row pairs][16 ky][32 ch][2 rows]
+// complex64 blocks: each row kernel reads and writes one contiguous 8 KB block,
+// each column kernel 64 contiguous 512-byte pieces.  The backward pass mirrors
+// this (row-backward, column-backward, and a per-mode kernel for the spectral
+// weight gradient, a GEMM over the batch), recomputing the projection's
+// hidden layer and the input features instead of storing them.
 #include <math.h>
 #include <cuda_bf16.h>
 
 #include <new>
 
 #include "common.cuh"
-#include "regfft.cuh"
 
 namespace cisor {
 
@@ -40,419 +60,927 @@ __host__ __device__ constexpr long long f_R(int l) { return F_LAYERS + l * F_LAY
 __host__ __device__ constexpr long long f_W(int l) { return f_R(l) + (long long)FMODES * FC * FC * 2; }
 __host__ __device__ constexpr long long f_B(int l) { return f_W(l) + FC * FC; }
 
+constexpr int RB = 2;              // image rows per row-kernel item
+constexpr int NP = RB * FN;        // pixels per item
+constexpr int NIB = FN / RB;       // row blocks per image
+constexpr int BLK = FM * FC * RB;  // complex values of one spectral row block [ky][c][r]
+constexpr int NTH = 256;           // threads of every FNO kernel
+constexpr int NPP = NP + 4;        // shared-memory pitch (floats) of one channel's NP pixels
+constexpr int PART_W = FC * FC + FC;                 // dW_l, db_l
+constexpr int PART_P = FH * FC + FH + 2 * FH + 2;    // dP1, dc1, dP2, dc2
+constexpr int PART_0 = FC * FIN + FC;                // dW0, db0
+constexpr int PART_MAX = PART_P;
+
+// DFT tables, FP64-built, as BF16 hi / lo pairs laid out so that every MMA
+// fragment register is ONE 32-bit load (the two BF16 values of a register are
+// adjacent along the contraction index) and, from shared memory, conflict-free:
+//   RowF  B operand [kyc][ix], pitch RFP: E(ix, kyc) = cos(2 pi ky ix / 128) (kyc = 2 ky), -sin (kyc = 2 ky + 1)
+//   RowI  B operand [ix][kyc], pitch RIP: the same values, transposed
+//   ColF  A operand [row][k] (64 x 256), pitch CFP: [[Fr, -Fi], [Fi, Fr]], F(kx, iy) = exp(-2 pi j kx' iy / 128)
+//   ColI  A operand [row][k] (256 x 64), pitch CIP: [[Fr, Fi], [-Fi, Fr]] (conj(F) transposed)
+// kx' = kx for kx < 16, kx + 96 otherwise.
+constexpr int RFP = FN + 8, RIP = 2 * FM + 8, CFP = 2 * FN + 8, CIP = 2 * FKX + 8;
+constexpr int T_RF = 2 * FM * RFP, T_RI = FN * RIP, T_CF = 2 * FKX * CFP, T_CI = 2 * FN * CIP;
+constexpr int T_ROW = 2 * (T_RF + T_RI);        // bf16 of the row tables (hi and lo), copied to shared memory
+constexpr int T_ALL = T_ROW + 2 * (T_CF + T_CI);  // + the column tables (read through L1)
+constexpr int WP = FC + 8;                        // pitch (bf16) of a 32-wide weight row in shared memory
+constexpr int P1TP = FH + 8;                      // pitch (bf16) of P1^T rows
+
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// ------------------------------------------------------------------ kernels
-
-__global__ void fno_features_lift(const float2* __restrict__ f, int f_per_sample, const float2* __restrict__ u_in,
-                                  const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ pm, int B,
-                                  float* __restrict__ feat, float* __restrict__ v0) {
-  __shared__ float W[FC * FIN], bb[FC];
-  for (int i = threadIdx.x; i < FC * FIN; i += blockDim.x) W[i] = __bfloat162float(wbf[F_W0 + i]);
-  for (int i = threadIdx.x; i < FC; i += blockDim.x) bb[i] = pm[F_B0 + i];
-  __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * FNN) return;
-  const int b = (int)(idx / FNN), pix = (int)(idx % FNN);
-  const int iy = pix / FN, ix = pix % FN;
-  const float2 fv = f[(f_per_sample ? (long long)b * FNN : 0) + pix];
-  const float2* ub = u_in + (long long)b * FNN;
-  const float2 u = ub[pix];
-  // central differences, clamped at the edges
-  const float2 gx = c_scale(c_sub(ub[iy * FN + min(ix + 1, FN - 1)], ub[iy * FN + max(ix - 1, 0)]), 0.5f);
-  const float2 gy = c_scale(c_sub(ub[min(iy + 1, FN - 1) * FN + ix], ub[max(iy - 1, 0) * FN + ix]), 0.5f);
-  const float vx = c_cjmul(u, gx).y, vy = c_cjmul(u, gy).y;
-  const float nv = sqrtf(vx * vx + vy * vy);
-  const float dx = nv > 0.f ? vx / nv : 0.f, dy = nv > 0.f ? vy / nv : 0.f;
-  const float a[FIN] = {fv.x, fv.y, u.x, u.y, dx, dy, (ix + 0.5f) / FN - 0.5f, (iy + 0.5f) / FN - 0.5f};
-#pragma unroll
-  for (int k = 0; k < FIN; ++k) feat[((long long)b * FIN + k) * FNN + pix] = a[k];
-#pragma unroll 4
-  for (int c = 0; c < FC; ++c) {
-    float s = bb[c];
-#pragma unroll
-    for (int k = 0; k < FIN; ++k) s += W[c * FIN + k] * a[k];
-    v0[((long long)b * FC + c) * FNN + pix] = s;
-  }
+// ------------------------------------------------------------------ tensor-core tiles
+// m16n8k16 fragments (PTX ISA, mma.sync .bf16): lane = 4 g + t;
+//   A (16 x 16): a0 a1 (row g, k 2t, 2t+1), a2 a3 (row g + 8), a4 a5 (row g, k 2t + 8, +9), a6 a7 (row g + 8)
+//   B (16 x 8):  b0 b1 (k 2t, 2t+1; col g), b2 b3 (k 2t + 8, +9; col g)
+//   D (16 x 8):  d0 d1 (row g, col 2t, 2t+1), d2 d3 (row g + 8)
+__device__ __forceinline__ uint32_t bf_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+  hi = bf_bits(h0) | (bf_bits(h1) << 16);
+  lo = bf_bits(__float2bfloat16_rn(x0 - __bfloat162float(h0))) |
+       (bf_bits(__float2bfloat16_rn(x1 - __bfloat162float(h1))) << 16);
 }
-
-// X[img][kx_idx*16 + ky] = wscale(ky) * sum v[iy][ix] exp(-2 pi j (kx iy + ky ix)/128), one CTA per image.
-// wscale(ky) = scale * (weighted && ky > 0 ? 2 : 1).
-__global__ void __launch_bounds__(256) fno_analysis(const float* __restrict__ v, float2* __restrict__ X,
-                                                    const float2* __restrict__ twst, float scale, int weighted) {
-  typedef TwTable<FN, false> TT;
-  constexpr int PP = FN + FN / 16;
-  __shared__ float2 tw[TT::SIZE];
-  __shared__ float2 xbuf[16 * PP];    // exchange buffer (rows, then columns)
-  __shared__ float2 colbuf[FN * FM];  // row-transform outputs ky < 16, column layout
-  const long long img = blockIdx.x;
-  const float* src = v + img * FNN;
-  for (int i = threadIdx.x; i < TT::SIZE; i += 256) tw[i] = twst[i];
-  const int lt = threadIdx.x & 15, row = threadIdx.x >> 4;
-  const ColLay<FM> clay{lt};
-  for (int r0 = 0; r0 < FN; r0 += 16) {
-    const int iy = r0 + row;
-    float2 x[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) x[r] = make_float2(src[iy * FN + lt + 16 * r], 0.f);
-    reg_fft<FN, false, false>(x, xbuf, RowLayA<FN>{row * PP}, RowLayB<FN>{row * PP}, lt, tw);
-    // output element lt (ky = lt) sits in x[0]
-    colbuf[ColLay<FM>{lt}(iy)] = x[0];
-  }
-  __syncthreads();
-  // column transforms: thread (w = ky, lt)
-  const int ky = threadIdx.x % FM, ct = threadIdx.x / FM;
-  const ColLay<FM> lay{ky};
-  float2 x[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) x[r] = colbuf[lay(ct + 16 * r)];
-  reg_fft<FN, false, false>(x, xbuf, lay, lay, ct, tw);
-  const float ws = scale * ((weighted && ky > 0) ? 2.f : 1.f);
-  // outputs: kx = ct in x[0], kx = 112 + ct in x[7]
-  float2* dst = X + img * FMODES;
-  dst[ct * FM + ky] = make_float2(x[0].x * ws, x[0].y * ws);
-  dst[(FM + ct) * FM + ky] = make_float2(x[7].x * ws, x[7].y * ws);
-  (void)clay;
+struct FragA {
+  uint32_t h[4], l[4];
+};
+struct FragB {
+  uint32_t h[2], l[2];
+};
+// A fragment of FP32 values A(m, k), split into BF16 hi + lo
+template <class F>
+__device__ __forceinline__ FragA load_a(F A, int m0, int k0, int g, int t) {
+  FragA f;
+  split_pair(A(m0 + g, k0 + 2 * t), A(m0 + g, k0 + 2 * t + 1), f.h[0], f.l[0]);
+  split_pair(A(m0 + g + 8, k0 + 2 * t), A(m0 + g + 8, k0 + 2 * t + 1), f.h[1], f.l[1]);
+  split_pair(A(m0 + g, k0 + 2 * t + 8), A(m0 + g, k0 + 2 * t + 9), f.h[2], f.l[2]);
+  split_pair(A(m0 + g + 8, k0 + 2 * t + 8), A(m0 + g + 8, k0 + 2 * t + 9), f.h[3], f.l[3]);
+  return f;
 }
-
-// s[iy][ix] (+)= scale * Re sum_{kx,ky} w_ky Y[kx][ky] exp(+2 pi j (kx iy + ky ix)/128), one CTA per image.
-__global__ void __launch_bounds__(256) fno_synthesis(const float2* __restrict__ Y, float* __restrict__ s,
-                                                     const float2* __restrict__ twst, float scale, int weighted,
-                                                     int accumulate) {
-  typedef TwTable<FN, true> TT;
-  constexpr int PP = FN + FN / 16;
-  __shared__ float2 tw[TT::SIZE];
-  __shared__ float2 xbuf[16 * PP];
-  __shared__ float2 colbuf[FN * FM];
-  const long long img = blockIdx.x;
-  for (int i = threadIdx.x; i < TT::SIZE; i += 256) tw[i] = twst[TW_STRIDE + i];
-  const float2* src = Y + img * FMODES;
-  // column inverse transforms (along iy) of the 32 kept kx modes, thread (w = ky, ct)
-  {
-    const int ky = threadIdx.x % FM, ct = threadIdx.x / FM;
-    const float ws = scale * ((weighted && ky > 0) ? 2.f : 1.f);
-    const ColLay<FM> lay{ky};
-    float2 x[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) x[r] = make_float2(0.f, 0.f);
-    // reversed plan for 128 starts with radix 2: input element ct + 16 q + 64 r sits in x[2 q + r]
-    const float2 a = src[ct * FM + ky], b = src[(FM + ct) * FM + ky];
-    x[0] = make_float2(a.x * ws, a.y * ws);             // kx = ct        (q = 0, r = 0)
-    x[7] = make_float2(b.x * ws, b.y * ws);             // kx = 112 + ct  (q = 3, r = 1)
-    reg_fft<FN, true, true>(x, xbuf, lay, lay, ct, tw);
-    // outputs iy = ct + 16 r in x[r]
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) colbuf[lay(ct + 16 * r)] = x[r];
-  }
-  __syncthreads();
-  float* dst = s + img * FNN;
-  const int lt = threadIdx.x & 15, row = threadIdx.x >> 4;
-  for (int r0 = 0; r0 < FN; r0 += 16) {
-    const int iy = r0 + row;
-    float2 x[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) x[r] = make_float2(0.f, 0.f);
-    x[0] = colbuf[ColLay<FM>{lt}(iy)];                   // ky = lt (element lt, q = 0, r = 0)
-    reg_fft<FN, true, true>(x, xbuf, RowLayA<FN>{row * PP}, RowLayB<FN>{row * PP}, lt, tw);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float* o = dst + iy * FN + lt + 16 * r;
-      *o = accumulate ? (*o + x[r].x) : x[r].x;
-    }
-  }
+// B fragment of FP32 values B(k, n), split into BF16 hi + lo
+template <class F>
+__device__ __forceinline__ FragB load_b(F B, int k0, int n0, int g, int t) {
+  FragB f;
+  split_pair(B(k0 + 2 * t, n0 + g), B(k0 + 2 * t + 1, n0 + g), f.h[0], f.l[0]);
+  split_pair(B(k0 + 2 * t + 8, n0 + g), B(k0 + 2 * t + 9, n0 + g), f.h[1], f.l[1]);
+  return f;
 }
-
-// Y[b][o][m] = sum_i R[m][i][o] X[b][i][m], one CTA per mode.
-__global__ void __launch_bounds__(256) fno_mix_fwd(const float2* __restrict__ X, const __nv_bfloat16* __restrict__ wbf,
-                                                   long long roff, int B, float2* __restrict__ Y) {
-  __shared__ float2 R[FC * FC];
-  __shared__ float2 Xm[64 * FC];
-  const int m = blockIdx.x;
-  const __nv_bfloat16* rw = wbf + roff + (long long)m * FC * FC * 2;
-  for (int e = threadIdx.x; e < FC * FC; e += 256)
-    R[e] = make_float2(__bfloat162float(rw[2 * e]), __bfloat162float(rw[2 * e + 1]));
-  for (int b0 = 0; b0 < B; b0 += 64) {
-    const int nb = min(64, B - b0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * FC; e += 256) {
-      const int b = e / FC, i = e % FC;
-      Xm[e] = X[((long long)(b0 + b) * FC + i) * FMODES + m];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * FC; e += 256) {
-      const int b = e / FC, o = e % FC;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 8
-      for (int i = 0; i < FC; ++i) acc = c_add(acc, c_mul(R[i * FC + o], Xm[b * FC + i]));
-      Y[((long long)(b0 + b) * FC + o) * FMODES + m] = acc;
-    }
-  }
+// B fragment from a BF16 matrix stored [n][k] (k pairs adjacent), pitch pw 32-bit words
+__device__ __forceinline__ void load_b_tab(const uint32_t* tab, int pw, int k0, int n0, int g, int t,
+                                           uint32_t (&b)[2]) {
+  const uint32_t* row = tab + (n0 + g) * pw + (k0 >> 1) + t;
+  b[0] = row[0];
+  b[1] = row[4];
 }
-
-// dX[b][i] = sum_o conj(R[i][o]) dY[b][o];  dR[m][i][o] += sum_b conj(X[b][i]) dY[b][o].
-__global__ void __launch_bounds__(256) fno_mix_bwd(const float2* __restrict__ X, const float2* __restrict__ dY,
-                                                   const __nv_bfloat16* __restrict__ wbf, long long roff, int B,
-                                                   float2* __restrict__ dX, float* __restrict__ grad) {
-  __shared__ float2 R[FC * FC];
-  __shared__ float2 Xm[64 * FC];
-  __shared__ float2 Gm[64 * FC];
-  const int m = blockIdx.x;
-  const __nv_bfloat16* rw = wbf + roff + (long long)m * FC * FC * 2;
-  for (int e = threadIdx.x; e < FC * FC; e += 256)
-    R[e] = make_float2(__bfloat162float(rw[2 * e]), __bfloat162float(rw[2 * e + 1]));
-  float2 dr[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  for (int b0 = 0; b0 < B; b0 += 64) {
-    const int nb = min(64, B - b0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * FC; e += 256) {
-      const int b = e / FC, i = e % FC;
-      Xm[e] = X[((long long)(b0 + b) * FC + i) * FMODES + m];
-      Gm[e] = dY[((long long)(b0 + b) * FC + i) * FMODES + m];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * FC; e += 256) {
-      const int b = e / FC, i = e % FC;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 8
-      for (int o = 0; o < FC; ++o) acc = c_add(acc, c_cjmul(R[i * FC + o], Gm[b * FC + o]));
-      dX[((long long)(b0 + b) * FC + i) * FMODES + m] = acc;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      const int i = e / FC, o = e % FC;
-      for (int b = 0; b < nb; ++b) dr[k] = c_add(dr[k], c_cjmul(Xm[b * FC + i], Gm[b * FC + o]));
-    }
-  }
-  float* g = grad + roff + (long long)m * FC * FC * 2;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int e = threadIdx.x + 256 * k;
-    g[2 * e] += dr[k].x;
-    g[2 * e + 1] += dr[k].y;
-  }
+// A fragment (hi and lo) from BF16 tables stored [m][k], pitch pw words, in global memory (read-only path)
+__device__ __forceinline__ FragA load_a_tab(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo, int pw,
+                                            int m0, int k0, int g, int t) {
+  FragA f;
+  const int o0 = (m0 + g) * pw + (k0 >> 1) + t, o1 = o0 + 8 * pw;
+  f.h[0] = __ldg(hi + o0);
+  f.h[1] = __ldg(hi + o1);
+  f.h[2] = __ldg(hi + o0 + 4);
+  f.h[3] = __ldg(hi + o1 + 4);
+  f.l[0] = __ldg(lo + o0);
+  f.l[1] = __ldg(lo + o1);
+  f.l[2] = __ldg(lo + o0 + 4);
+  f.l[3] = __ldg(lo + o1 + 4);
+  return f;
 }
-
-// pre = s + W v_prev + b (pre holds s on entry), v_out = GELU(pre) or pre; one thread per pixel.
-__global__ void __launch_bounds__(128) fno_pointwise_fwd(float* __restrict__ pre, const float* __restrict__ vprev,
-                                                         const __nv_bfloat16* __restrict__ wbf, const float* __restrict__ pm,
-                                                         long long woff, long long boff, int B, int act,
-                                                         float* __restrict__ vout) {
-  __shared__ float W[FC * FC], bb[FC];
-  for (int i = threadIdx.x; i < FC * FC; i += blockDim.x) W[i] = __bfloat162float(wbf[woff + i]);
-  for (int i = threadIdx.x; i < FC; i += blockDim.x) bb[i] = pm[boff + i];
-  __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * FNN) return;
-  const long long b = idx / FNN, pix = idx % FNN;
-  const float* vp = vprev + b * FC * FNN + pix;
-  float vin[FC];
-#pragma unroll
-  for (int i = 0; i < FC; ++i) vin[i] = vp[(long long)i * FNN];
-  float* pp = pre + b * FC * FNN + pix;
-  float* vo = vout + b * FC * FNN + pix;
-#pragma unroll 4
-  for (int o = 0; o < FC; ++o) {
-    float acc = pp[(long long)o * FNN] + bb[o];
-#pragma unroll
-    for (int i = 0; i < FC; ++i) acc += W[o * FC + i] * vin[i];
-    pp[(long long)o * FNN] = acc;
-    vo[(long long)o * FNN] = act ? gelu_f(acc) : acc;
-  }
-}
-
-// dpre = dv * GELU'(pre) (or dv), dv_prev = W^T dpre; one thread per pixel.
-__global__ void __launch_bounds__(128) fno_pointwise_bwd(const float* __restrict__ dv, const float* __restrict__ pre,
-                                                         const __nv_bfloat16* __restrict__ wbf, long long woff, int B,
-                                                         int act, float* __restrict__ dpre, float* __restrict__ dvprev) {
-  __shared__ float W[FC * FC];
-  for (int i = threadIdx.x; i < FC * FC; i += blockDim.x) W[i] = __bfloat162float(wbf[woff + i]);
-  __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * FNN) return;
-  const long long b = idx / FNN, pix = idx % FNN;
-  const long long base = b * FC * FNN + pix;
-  float acc[FC];
-#pragma unroll
-  for (int i = 0; i < FC; ++i) acc[i] = 0.f;
-#pragma unroll 2
-  for (int o = 0; o < FC; ++o) {
-    float d = dv[base + (long long)o * FNN];
-    if (act) d *= gelu_grad_f(pre[base + (long long)o * FNN]);
-    dpre[base + (long long)o * FNN] = d;
-#pragma unroll
-    for (int i = 0; i < FC; ++i) acc[i] += W[o * FC + i] * d;
-  }
-#pragma unroll
-  for (int i = 0; i < FC; ++i) dvprev[base + (long long)i * FNN] = acc[i];
-}
-
-// z = P1 v + c1, h = GELU(z), out = P2 h + c2; one thread per pixel.
-__global__ void __launch_bounds__(128) fno_proj_fwd(const float* __restrict__ vL, const __nv_bfloat16* __restrict__ wbf,
-                                                    const float* __restrict__ pm, int B, float* __restrict__ z,
-                                                    float* __restrict__ h, float2* __restrict__ out) {
-  __shared__ float P1[FH * FC], P2[2 * FH], c1[FH];
-  for (int i = threadIdx.x; i < FH * FC; i += blockDim.x) P1[i] = __bfloat162float(wbf[F_P1 + i]);
-  for (int i = threadIdx.x; i < 2 * FH; i += blockDim.x) P2[i] = __bfloat162float(wbf[F_P2 + i]);
-  for (int i = threadIdx.x; i < FH; i += blockDim.x) c1[i] = pm[F_C1 + i];
-  __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * FNN) return;
-  const long long b = idx / FNN, pix = idx % FNN;
-  float vin[FC];
-#pragma unroll
-  for (int i = 0; i < FC; ++i) vin[i] = vL[(b * FC + i) * FNN + pix];
-  float o0 = pm[F_C2], o1 = pm[F_C2 + 1];
-#pragma unroll 2
-  for (int k = 0; k < FH; ++k) {
-    float acc = c1[k];
-#pragma unroll
-    for (int i = 0; i < FC; ++i) acc += P1[k * FC + i] * vin[i];
-    const float hv = gelu_f(acc);
-    z[(b * FH + k) * FNN + pix] = acc;
-    h[(b * FH + k) * FNN + pix] = hv;
-    o0 += P2[k] * hv;
-    o1 += P2[FH + k] * hv;
-  }
-  out[b * FNN + pix] = make_float2(o0, o1);
-}
-
-// Tensor-core projection: z = P1 v + c1 on mma.sync m16n8k16 (BF16 operands,
-// FP32 accumulation), h = GELU(z), out = P2 h + c2.  A warp owns 16 pixels x
-// 128 hidden units (16 n-tiles, K = 32 channels in two k-steps).  Activations
-// are split into BF16 hi + lo parts (two MMAs), so the product keeps ~16
-// mantissa bits of v; the BF16 weights are exact.  store != 0 keeps z and h
-// for the backward pass.
-__device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
-  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_col));
-  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_col));
-  return a | (b << 16);
-}
-__device__ __forceinline__ float bf16_residual(float x) { return x - __bfloat162float(__float2bfloat16_rn(x)); }
-
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// d += A B with both operands split (three products; lo x lo is below FP32 rounding)
+__device__ __forceinline__ void mma3(float (&d)[4], const FragA& a, const FragB& b) {
+  mma16816(d, a.h, b.h);
+  mma16816(d, a.l, b.h);
+  mma16816(d, a.h, b.l);
+}
+__device__ __forceinline__ void mma3t(float (&d)[4], const FragA& a, const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+  mma16816(d, a.h, bh);
+  mma16816(d, a.l, bh);
+  mma16816(d, a.h, bl);
+}
+// d += A B with an exact BF16 B (weights)
+__device__ __forceinline__ void mma2(float (&d)[4], const FragA& a, const uint32_t (&b)[2]) {
+  mma16816(d, a.h, b);
+  mma16816(d, a.l, b);
 }
 
-template <int STORE>
-__global__ void __launch_bounds__(128) fno_proj_fwd_tc(const float* __restrict__ vL,
-                                                       const __nv_bfloat16* __restrict__ wbf,
-                                                       const float* __restrict__ pm, int B, float* __restrict__ z,
-                                                       float* __restrict__ h, float2* __restrict__ out) {
-  __shared__ uint32_t P1w[FH * FC / 2];  // P1[n][k] as bf16 pairs along k
-  __shared__ float P2s[2 * FH], c1s[FH];
-  const uint32_t* p1g = reinterpret_cast<const uint32_t*>(wbf + F_P1);
-  for (int i = threadIdx.x; i < FH * FC / 2; i += 128) P1w[i] = p1g[i];
-  for (int i = threadIdx.x; i < 2 * FH; i += 128) P2s[i] = __bfloat162float(wbf[F_P2 + i]);
-  for (int i = threadIdx.x; i < FH; i += 128) c1s[i] = pm[F_C1 + i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const long long P0 = ((long long)blockIdx.x * 4 + warp) * 16;  // first pixel of this warp
-  if (P0 >= (long long)B * FNN) return;
-  const long long b = P0 / FNN;
-  const int pix0 = (int)(P0 % FNN);  // 16 pixels never straddle samples (FNN % 16 == 0)
-  const float* vb = vL + b * FC * FNN + pix0;
-  // A fragments (hi and lo) for the two k-steps
-  uint32_t ahi[2][4], alo[2][4];
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+// bytes (multiple of 16, both 16-byte aligned) from global to shared by the whole CTA
+__device__ __forceinline__ void cta_copy(void* dst, const void* src, int bytes) {
+  for (int i = threadIdx.x * 16; i < bytes; i += NTH * 16) cp16((char*)dst + i, (const char*)src + i);
+}
+// a [FC][NP] block of sample b's planar [B][FC][FNN] field (pixels pix0 ..) into shared memory, pitch NPP
+__device__ __forceinline__ void load_planar(float* dst, const float* src, int b, long long pix0) {
+  for (int i = threadIdx.x; i < FC * NP / 4; i += NTH) {
+    const int c = i / (NP / 4), q = i % (NP / 4);
+    cp16(dst + c * NPP + 4 * q, src + ((long long)b * FC + c) * FNN + pix0 + 4 * q);
+  }
+}
+// a 32 x 32 BF16 weight matrix W[o][i] into shared memory, as Ws[o][i] (pitch WP) and / or Wt[i][o]
+__device__ __forceinline__ void load_w(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* ws, __nv_bfloat16* wt) {
+  for (int e = threadIdx.x; e < FC * FC; e += NTH) {
+    const int o = e / FC, i = e % FC;
+    const __nv_bfloat16 v = w[e];
+    if (ws) ws[o * WP + i] = v;
+    if (wt) wt[i * WP + o] = v;
+  }
+}
+
+// ------------------------------------------------------------------ shared phases of the row kernels
+__device__ __forceinline__ const uint32_t* tab_rf(const __nv_bfloat16* tb, int lo) {
+  return reinterpret_cast<const uint32_t*>(tb + lo * T_RF);
+}
+__device__ __forceinline__ const uint32_t* tab_ri(const __nv_bfloat16* tb, int lo) {
+  return reinterpret_cast<const uint32_t*>(tb + 2 * T_RF + lo * T_RI);
+}
+
+// S(rr, ix) = Re sum_ky Z[ky][c][r] exp(+2 pi j ky ix / 128), rr = 32 r + c: GEMM
+// M = 64 (rr), N = 128 (ix), K = 32 (Re / Im of the 16 ky).  Adds into
+// dst[c * NPP + r * FN + ix] (accumulate) or stores there.
+__device__ __forceinline__ void row_inverse(const float2* zs, const __nv_bfloat16* tb, float* dst, bool accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const float* zf = reinterpret_cast<const float*>(zs);
+  auto A = [&](int rr, int k) { return zf[(((k >> 1) * FC + (rr & 31)) * RB + (rr >> 5)) * 2 + (k & 1)]; };
+  const uint32_t *th = tab_ri(tb, 0), *tl = tab_ri(tb, 1);
+  const int mt = warp & 3, nt0 = (warp >> 2) * 8;
+  float d[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
 #pragma unroll
   for (int ks = 0; ks < 2; ++ks) {
-    const int k0 = ks * 16 + 2 * t;
-    float x[8];
-    x[0] = vb[(long long)(k0)*FNN + g];
-    x[1] = vb[(long long)(k0 + 1) * FNN + g];
-    x[2] = vb[(long long)(k0)*FNN + g + 8];
-    x[3] = vb[(long long)(k0 + 1) * FNN + g + 8];
-    x[4] = vb[(long long)(k0 + 8) * FNN + g];
-    x[5] = vb[(long long)(k0 + 9) * FNN + g];
-    x[6] = vb[(long long)(k0 + 8) * FNN + g + 8];
-    x[7] = vb[(long long)(k0 + 9) * FNN + g + 8];
+    const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      ahi[ks][r] = pack_bf16(x[2 * r], x[2 * r + 1]);
-      alo[ks][r] = pack_bf16(bf16_residual(x[2 * r]), bf16_residual(x[2 * r + 1]));
+    for (int j = 0; j < 8; ++j) {
+      uint32_t bh[2], bl[2];
+      load_b_tab(th, RIP / 2, 16 * ks, 8 * (nt0 + j), g, t, bh);
+      load_b_tab(tl, RIP / 2, 16 * ks, 8 * (nt0 + j), g, t, bl);
+      mma3t(d[j], a, bh, bl);
     }
   }
-  float o0a = 0.f, o1a = 0.f, o0b = 0.f, o1b = 0.f;  // outputs of pixels g (a) and g + 8 (b)
-#pragma unroll 4
-  for (int j = 0; j < FH / 8; ++j) {
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-    const int n = 8 * j + g;
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      const uint32_t b0 = P1w[n * (FC / 2) + ks * 8 + t];      // k = ks*16 + 2t, 2t+1
-      const uint32_t b1 = P1w[n * (FC / 2) + ks * 8 + 4 + t];  // k + 8
-      mma_bf16_16816(d, ahi[ks], b0, b1);
-      mma_bf16_16816(d, alo[ks], b0, b1);
-    }
-    // d[0], d[1]: pixel g, hidden 8j + 2t, +1 ; d[2], d[3]: pixel g + 8
+  for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int hh = 8 * j + 2 * t + (e & 1);
-      const int px = g + (e >> 1) * 8;
-      const float zz = d[e] + c1s[hh];
-      const float hv = gelu_f(zz);
-      if (STORE) {
-        z[(b * FH + hh) * FNN + pix0 + px] = zz;
-        h[(b * FH + hh) * FNN + pix0 + px] = hv;
-      }
-      if (e < 2) {
-        o0a += P2s[hh] * hv;
-        o1a += P2s[FH + hh] * hv;
-      } else {
-        o0b += P2s[hh] * hv;
-        o1b += P2s[FH + hh] * hv;
-      }
+      const int rr = 16 * mt + g + (e >> 1) * 8, ix = 8 * (nt0 + j) + 2 * t + (e & 1);
+      float* p = dst + (rr & 31) * NPP + (rr >> 5) * FN + ix;
+      *p = accumulate ? *p + d[j][e] : d[j][e];
+    }
+}
+
+// T[ky][c][r] = sum_ix src[c * NPP + r * FN + ix] exp(-2 pi j ky ix / 128): GEMM
+// M = 64 (rr), N = 32 (Re / Im of 16 ky), K = 128 (ix); result in stage [BLK].
+__device__ __forceinline__ void row_forward(const float* src, const __nv_bfloat16* tb, float2* stage) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  auto A = [&](int rr, int ix) { return src[(rr & 31) * NPP + (rr >> 5) * FN + ix]; };
+  const uint32_t *th = tab_rf(tb, 0), *tl = tab_rf(tb, 1);
+  const int mt = warp & 3, nt0 = (warp >> 2) * 2;
+  float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll 2
+  for (int ks = 0; ks < FN / 16; ++ks) {
+    const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint32_t bh[2], bl[2];
+      load_b_tab(th, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bh);
+      load_b_tab(tl, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bl);
+      mma3t(d[j], a, bh, bl);
     }
   }
-  // sum over the four lanes (t) that share a pixel row g
 #pragma unroll
-  for (int m = 1; m < 4; m <<= 1) {
-    o0a += __shfl_xor_sync(0xffffffffu, o0a, m);
-    o1a += __shfl_xor_sync(0xffffffffu, o1a, m);
-    o0b += __shfl_xor_sync(0xffffffffu, o0b, m);
-    o1b += __shfl_xor_sync(0xffffffffu, o1b, m);
-  }
-  if (t == 0) {
-    const float c20 = pm[F_C2], c21 = pm[F_C2 + 1];
-    out[b * FNN + pix0 + g] = make_float2(o0a + c20, o1a + c21);
-    out[b * FNN + pix0 + g + 8] = make_float2(o0b + c20, o1b + c21);
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rr = 16 * mt + g + 8 * h, ky = 4 * (nt0 + j) + t;
+      stage[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[j][2 * h], d[j][2 * h + 1]);
+    }
+}
+
+// out[p][o] (+)= sum_i A(p, i) W[o][i] over the NP pixels (M = NP, N = FC, K = FC), W exact BF16 in
+// ws ([o][i], pitch WP); epi(p, o, value) consumes each result once.
+template <class FA, class Epi>
+__device__ __forceinline__ void pixel_mix(FA A, const __nv_bfloat16* ws, Epi epi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(ws);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int mt = 2 * warp + h;
+    const FragA a0 = load_a(A, 16 * mt, 0, g, t), a1 = load_a(A, 16 * mt, 16, g, t);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      uint32_t b0[2], b1[2];
+      load_b_tab(w32, WP / 2, 0, 8 * nt, g, t, b0);
+      load_b_tab(w32, WP / 2, 16, 8 * nt, g, t, b1);
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma2(d, a0, b0);
+      mma2(d, a1, b1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) epi(16 * mt + g + (e >> 1) * 8, 8 * nt + 2 * t + (e & 1), d[e]);
+    }
   }
 }
 
-// dz = (P2^T dout) * GELU'(z) (overwrites z), dv = P1^T dz; one thread per pixel.
-__global__ void __launch_bounds__(128) fno_proj_bwd(const float* __restrict__ dout, float* __restrict__ z,
-                                                    const __nv_bfloat16* __restrict__ wbf, int B,
-                                                    float* __restrict__ dvL) {
-  __shared__ float P1[FH * FC], P2[2 * FH];
-  for (int i = threadIdx.x; i < FH * FC; i += blockDim.x) P1[i] = __bfloat162float(wbf[F_P1 + i]);
-  for (int i = threadIdx.x; i < 2 * FH; i += blockDim.x) P2[i] = __bfloat162float(wbf[F_P2 + i]);
+// the 8 input features of the NP pixels of rows iy0, iy0 + 1 into as[k * NPP + p]
+// (us: rows iy0 - 1 .. iy0 + RB clamped, fs: rows iy0 .. iy0 + RB - 1)
+__device__ __forceinline__ void features(const float2* us, const float2* fs, int iy0, float* as) {
+  for (int p = threadIdx.x; p < NP; p += NTH) {
+    const int r = p / FN, ix = p % FN;
+    const float2 u = us[(r + 1) * FN + ix];
+    const float2 gx = c_scale(c_sub(us[(r + 1) * FN + min(ix + 1, FN - 1)], us[(r + 1) * FN + max(ix - 1, 0)]), 0.5f);
+    const float2 gy = c_scale(c_sub(us[(r + 2) * FN + ix], us[r * FN + ix]), 0.5f);
+    const float vx = c_cjmul(u, gx).y, vy = c_cjmul(u, gy).y;
+    const float nv = sqrtf(vx * vx + vy * vy);
+    const float2 fv = fs[p];
+    as[0 * NPP + p] = fv.x;
+    as[1 * NPP + p] = fv.y;
+    as[2 * NPP + p] = u.x;
+    as[3 * NPP + p] = u.y;
+    as[4 * NPP + p] = nv > 0.f ? vx / nv : 0.f;
+    as[5 * NPP + p] = nv > 0.f ? vy / nv : 0.f;
+    as[6 * NPP + p] = (ix + 0.5f) / FN - 0.5f;
+    as[7 * NPP + p] = (iy0 + r + 0.5f) / FN - 0.5f;
+  }
+}
+
+// rows iy0 - 1 .. iy0 + RB of u_in (clamped) and rows iy0 .. of f into shared memory
+__device__ __forceinline__ void load_inputs(const float2* u_in, const float2* f, int fps, int b, int iy0, float2* us,
+                                            float2* fs) {
+#pragma unroll
+  for (int r = 0; r < RB + 2; ++r) {
+    const int iy = min(max(iy0 - 1 + r, 0), FN - 1);
+    cta_copy(us + r * FN, u_in + (long long)b * FNN + iy * FN, FN * 8);
+  }
+  cta_copy(fs, f + (fps ? (long long)b * FNN : 0) + iy0 * FN, NP * 8);
+}
+
+// float4-wide elementwise pass over a [FC][NPP] shared block and its global [FC][FNN] rows
+template <class Op>
+__device__ __forceinline__ void planar_pass(float* sm, long long gbase, Op op) {
+  for (int i = threadIdx.x; i < FC * NP / 4; i += NTH) {
+    const int c = i / (NP / 4), q = i % (NP / 4);
+    op(reinterpret_cast<float4*>(sm + c * NPP)[q], gbase + (long long)c * FNN + 4 * q);
+  }
+}
+
+// ------------------------------------------------------------------ forward kernels
+// v0 = W0 a + b0 (lifting), v0 to global, and its row DFT (the first column kernel's input).
+constexpr int SM_LIFT = (FC * NPP + FIN * NPP) * 4 + ((RB + 2) * FN + NP + BLK) * 8 + T_ROW * 2;
+__global__ void __launch_bounds__(NTH, 2) fno_lift_fwd(const float2* __restrict__ f, int fps,
+                                                       const float2* __restrict__ u_in,
+                                                       const __nv_bfloat16* __restrict__ wbf,
+                                                       const float* __restrict__ pm,
+                                                       const __nv_bfloat16* __restrict__ tabs,
+                                                       float* __restrict__ v0, float2* __restrict__ T1) {
+  extern __shared__ __align__(16) float smem[];
+  float* ps = smem;                                         // [FC][NPP] v0
+  float* as = ps + FC * NPP;                                // [FIN][NPP] features
+  float2* us = reinterpret_cast<float2*>(as + FIN * NPP);   // [(RB + 2) FN]
+  float2* fs = us + (RB + 2) * FN;                          // [NP]
+  float2* stage = fs + NP;                                  // [BLK]
+  __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(stage + BLK);  // [T_ROW]
+  __shared__ __nv_bfloat16 w0[FC * FIN];
+  __shared__ float b0[FC];
+  const int b = blockIdx.y, iyb = blockIdx.x, iy0 = iyb * RB;
+  load_inputs(u_in, f, fps, b, iy0, us, fs);
+  cta_copy(tb, tabs, T_ROW * 2);
+  for (int i = threadIdx.x; i < FC * FIN; i += NTH) w0[i] = wbf[F_W0 + i];
+  if (threadIdx.x < FC) b0[threadIdx.x] = pm[F_B0 + threadIdx.x];
+  cp_wait_all();
   __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * FNN) return;
-  const long long b = idx / FNN, pix = idx % FNN;
-  const float d0 = dout[(b * 2) * FNN + pix], d1 = dout[(b * 2 + 1) * FNN + pix];
-  float acc[FC];
+  features(us, fs, iy0, as);
+  __syncthreads();
+  {  // GEMM M = NP, N = FC, K = 16 (8 features, zero padded)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    auto A = [&](int p, int k) { return k < FIN ? as[k * NPP + p] : 0.f; };
 #pragma unroll
-  for (int i = 0; i < FC; ++i) acc[i] = 0.f;
+    for (int i = 0; i < 2; ++i) {
+      const int mt = 2 * warp + i;
+      const FragA a = load_a(A, 16 * mt, 0, g, t);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = 8 * nt + g;
+        uint32_t bb[2];
+        bb[0] = bf_bits(w0[c * FIN + 2 * t]) | (bf_bits(w0[c * FIN + 2 * t + 1]) << 16);
+        bb[1] = 0u;  // k >= 8: zero padding
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma2(d, a, bb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = 16 * mt + g + (e >> 1) * 8, cc = 8 * nt + 2 * t + (e & 1);
+          ps[cc * NPP + p] = d[e] + b0[cc];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  planar_pass(ps, (long long)b * FC * FNN + (long long)iy0 * FN,
+              [&](float4& x, long long gi) { *reinterpret_cast<float4*>(v0 + gi) = x; });
+  row_forward(ps, tb, stage);
+  __syncthreads();
+  float4* dst = reinterpret_cast<float4*>(T1 + ((long long)b * NIB + iyb) * BLK);
+  for (int i = threadIdx.x; i < BLK / 2; i += NTH) dst[i] = reinterpret_cast<float4*>(stage)[i];
+}
+
+// Layer l: pre = Lsyn(Y) + W v + b (Lsyn: row inverse of the column kernel's Z),
+// v_{l+1} = GELU(pre) (or pre), then either the row DFT of v_{l+1} for the
+// next layer (PROJ = 0) or the projection out = P2 GELU(P1 v + c1) + c2 and,
+// when x0 is given, the warm start x0 = u_in (1 + out_0 + j out_1) (PROJ = 1).
+// Persistent over (sample, row block) items: the tables and weights are
+// staged once per CTA, and the next item's v_l and Z blocks are copied in
+// (cp.async) while the current item's activation, row DFT or projection runs.
+constexpr int SM_ROW = (2 * FC * NPP + FC) * 4 + BLK * 8 + T_ROW * 2 + FC * WP * 2;
+template <int PROJ>
+__global__ void __launch_bounds__(NTH, 2) fno_row_fwd(const float* __restrict__ vin, const float2* __restrict__ Z,
+                                                      const __nv_bfloat16* __restrict__ wbf,
+                                                      const float* __restrict__ pm, long long woff, long long boff,
+                                                      const __nv_bfloat16* __restrict__ tabs, int act, int B,
+                                                      float* __restrict__ pre_out, float* __restrict__ vout,
+                                                      float2* __restrict__ T1, float2* __restrict__ out,
+                                                      const float2* __restrict__ u_in, float2* __restrict__ x0) {
+  extern __shared__ __align__(16) float smem[];
+  float* vs = smem;                                        // [FC][NPP] v_l
+  float* ps = vs + FC * NPP;                               // [FC][NPP] pre, then v_{l+1}
+  float* bias = ps + FC * NPP;                             // [FC]
+  float2* zs = reinterpret_cast<float2*>(bias + FC);       // [BLK] Z block
+  __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(zs + BLK);  // [T_ROW]; P1, c1, P2 in the RowF part (PROJ)
+  __nv_bfloat16* ws = tb + T_ROW;                          // [FC][WP] W_l
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int items = B * NIB;
+  auto fetch = [&](int it) {
+    const int b = it / NIB, iyb = it % NIB;
+    load_planar(vs, vin, b, (long long)iyb * RB * FN);
+    cta_copy(zs, Z + ((long long)b * NIB + iyb) * BLK, BLK * 8);
+  };
+  if (blockIdx.x >= items) return;
+  cta_copy(tb + (PROJ ? 2 * T_RF : 0), tabs + (PROJ ? 2 * T_RF : 0), (PROJ ? 2 * T_RI : T_ROW) * 2);
+  fetch(blockIdx.x);
+  load_w(wbf + woff, ws, nullptr);
+  if (threadIdx.x < FC) bias[threadIdx.x] = pm[boff + threadIdx.x];
+  // projection weights in the (unused) RowF part of the table area: P1 [FH][WP], c1 [FH], P2 [2][FH]
+  __nv_bfloat16* p1 = tb;
+  float* c1 = reinterpret_cast<float*>(p1 + FH * WP);
+  float* p2 = c1 + FH;
+  if (PROJ) {
+    for (int e = threadIdx.x; e < FH * FC; e += NTH) p1[(e / FC) * WP + e % FC] = wbf[F_P1 + e];
+    for (int i = threadIdx.x; i < FH; i += NTH) c1[i] = pm[F_C1 + i];
+    for (int i = threadIdx.x; i < 2 * FH; i += NTH) p2[i] = __bfloat162float(wbf[F_P2 + i]);
+  }
+  cp_wait_all();
+  __syncthreads();
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = it / NIB, iyb = it % NIB, iy0 = iyb * RB;
+    const long long pix0 = (long long)iy0 * FN;
+    const long long gbase = (long long)b * FC * FNN + pix0;
+    row_inverse(zs, tb, ps, false);
+    __syncthreads();
+    pixel_mix([&](int p, int i) { return vs[i * NPP + p]; }, ws,
+              [&](int p, int o, float v) { ps[o * NPP + p] += v + bias[o]; });
+    __syncthreads();
+    const int nxt = it + gridDim.x;
+    if (nxt < items) fetch(nxt);  // vs and zs are free until the end of this item
+    // pre to global (training), activation in place, v_{l+1} to global
+    planar_pass(ps, gbase, [&](float4& x, long long gi) {
+      if (pre_out) *reinterpret_cast<float4*>(pre_out + gi) = x;
+      if (act) x = make_float4(gelu_f(x.x), gelu_f(x.y), gelu_f(x.z), gelu_f(x.w));
+      if (vout) *reinterpret_cast<float4*>(vout + gi) = x;
+    });
+    __syncthreads();
+    if (!PROJ) {  // the row DFT of v_{l+1}, written to the block's T1 slot from the fragments
+      float2* dst = T1 + ((long long)b * NIB + iyb) * BLK;
+      auto A = [&](int rr, int ix) { return ps[(rr & 31) * NPP + (rr >> 5) * FN + ix]; };
+      const uint32_t *th = tab_rf(tb, 0), *tl = tab_rf(tb, 1);
+      const int mt = warp & 3, nt0 = (warp >> 2) * 2;
+      float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll 2
-  for (int k = 0; k < FH; ++k) {
-    float* zp = z + (b * FH + k) * FNN + pix;
-    const float dz = (P2[k] * d0 + P2[FH + k] * d1) * gelu_grad_f(*zp);
-    *zp = dz;
+      for (int ks = 0; ks < FN / 16; ++ks) {
+        const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
 #pragma unroll
-    for (int i = 0; i < FC; ++i) acc[i] += P1[k * FC + i] * dz;
+        for (int j = 0; j < 2; ++j) {
+          uint32_t bh[2], bl[2];
+          load_b_tab(th, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bh);
+          load_b_tab(tl, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bl);
+          mma3t(d[j], a, bh, bl);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rr = 16 * mt + g + 8 * h, ky = 4 * (nt0 + j) + t;
+          dst[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[j][2 * h], d[j][2 * h + 1]);
+        }
+    } else {  // projection: z = P1 v + c1 (GEMM M = NP, N = FH, K = FC), h = GELU(z), out = P2 h + c2
+      auto A = [&](int p, int c) { return ps[c * NPP + p]; };
+      const uint32_t* p132 = reinterpret_cast<const uint32_t*>(p1);
+      const float c20 = pm[F_C2], c21 = pm[F_C2 + 1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int mt = 2 * warp + h;
+        const FragA a0 = load_a(A, 16 * mt, 0, g, t), a1 = load_a(A, 16 * mt, 16, g, t);
+        float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [row g / g + 8][out 0 / 1]
+#pragma unroll 4
+        for (int nt = 0; nt < FH / 8; ++nt) {
+          uint32_t b0[2], b1[2];
+          load_b_tab(p132, WP / 2, 0, 8 * nt, g, t, b0);
+          load_b_tab(p132, WP / 2, 16, 8 * nt, g, t, b1);
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+          mma2(d, a0, b0);
+          mma2(d, a1, b1);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int hid = 8 * nt + 2 * t + (e & 1);
+            const float hv = gelu_f(d[e] + c1[hid]);
+            o[e >> 1][0] += p2[hid] * hv;
+            o[e >> 1][1] += p2[FH + hid] * hv;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            o[r][k] += __shfl_xor_sync(0xffffffffu, o[r][k], 1);
+            o[r][k] += __shfl_xor_sync(0xffffffffu, o[r][k], 2);
+          }
+        if (t == 0)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const long long pix = (long long)b * FNN + pix0 + 16 * mt + g + 8 * r;
+            const float2 e = make_float2(o[r][0] + c20, o[r][1] + c21);
+            if (out) out[pix] = e;
+            if (x0) {
+              const float2 u = u_in[pix];
+              x0[pix] = c_add(u, c_mul(u, e));
+            }
+          }
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+  }
+}
+
+// Column kernel, one (ky, sample): X = ColF(T1) over iy to the 32 kept kx; forward: Y = mix_R(X) x w_ky / 128^2,
+// Z = ColI(Y); backward (BWD = 1, T1 = dT): dY = ColF(dT) x w_ky / 128^2, dX = mix_R^H(dY), dU = ColI(dX).
+// Xst (may be null) receives X (forward) or dY (backward) mode-major [mode][B][FC] for the weight gradient.
+constexpr int TSP = FN + 4;   // shared pitch (complex) of a channel's 128 rows
+constexpr int XSP = FC + 1;   // shared pitch (complex) of a mode's 32 channels
+constexpr int SM_COL = (FC * TSP + 2 * FKX * XSP) * 8;
+template <int BWD>
+__global__ void __launch_bounds__(NTH, 2) fno_col(const float2* __restrict__ Tin,
+                                                  const __nv_bfloat16* __restrict__ tabs,
+                                                  const __nv_bfloat16* __restrict__ wbf, long long roff, int B,
+                                                  float2* __restrict__ Xst, float2* __restrict__ Zout) {
+  extern __shared__ __align__(16) float smem[];
+  float2* ts = reinterpret_cast<float2*>(smem);  // [FC][TSP]: T(iy, c) at c * TSP + iy
+  float2* xs = ts + FC * TSP;                    // [FKX][XSP]
+  float2* ys = xs + FKX * XSP;                   // [FKX][XSP]
+  const int ky = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  // the block's column: 64 row pairs x 32 channels of 16 bytes ([iyb][ky][c][r] in global memory)
+  for (int i = threadIdx.x; i < NIB * FC; i += NTH) {
+    const int iyb = i / FC, c = i % FC;
+    cp16(ts + c * TSP + iyb * RB, Tin + ((long long)b * NIB + iyb) * BLK + (ky * FC + c) * RB);
+  }
+  cp_wait_all();
+  __syncthreads();
+  const float scale = (ky ? 2.f : 1.f) / FNN;
+  const uint32_t* cfh = reinterpret_cast<const uint32_t*>(tabs + T_ROW);
+  const uint32_t* cfl = cfh + T_CF / 2;
+  const uint32_t* cih = cfl + T_CF / 2;
+  const uint32_t* cil = cih + T_CI / 2;
+  {  // ColF: [Xr; Xi] (64 x 32) = [[Fr, -Fi], [Fi, Fr]] (64 x 256) [Tr; Ti] (256 x 32)
+    const float* tf = reinterpret_cast<const float*>(ts);
+    auto Bt = [&](int k, int c) { return tf[2 * (c * TSP + (k & 127)) + (k >> 7)]; };
+    const int mt = warp & 3, nt0 = (warp >> 2) * 2;
+    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll 2
+    for (int ks = 0; ks < 16; ++ks) {
+      const FragA a = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 16 * ks, g, t);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) mma3(d[j], a, load_b(Bt, 16 * ks, 8 * (nt0 + j), g, t));
+    }
+    float* xf = reinterpret_cast<float*>(xs);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = 16 * mt + g + (e >> 1) * 8, c = 8 * (nt0 + j) + 2 * t + (e & 1);
+        xf[((row & 31) * XSP + c) * 2 + (row >> 5)] = BWD ? d[j][e] * scale : d[j][e];
+      }
+  }
+  __syncthreads();
+  if (Xst)
+    for (int i = threadIdx.x; i < FKX * FC; i += NTH) {
+      const int kx = i / FC, c = i % FC;
+      Xst[((long long)(kx * FM + ky) * B + b) * FC + c] = xs[kx * XSP + c];
+    }
+  // per-mode mixing on the FP32 pipes, warp per kx, lane = output channel
+  for (int kx = warp; kx < FKX; kx += NTH / 32) {
+    const __nv_bfloat162* R = reinterpret_cast<const __nv_bfloat162*>(wbf + roff) + (long long)(kx * FM + ky) * FC * FC;
+    float2 acc = make_float2(0.f, 0.f);
+    if (!BWD) {  // Y[o] = sum_c X[c] R[c][o]
+#pragma unroll 8
+      for (int c = 0; c < FC; ++c) acc = c_fma(xs[kx * XSP + c], __bfloat1622float2(R[c * FC + lane]), acc);
+      ys[kx * XSP + lane] = c_scale(acc, scale);
+    } else {     // dX[c] = sum_o conj(R[c][o]) dY[o], lane = c
+#pragma unroll 8
+      for (int o = 0; o < FC; ++o) acc = c_cjfma(__bfloat1622float2(R[lane * FC + o]), xs[kx * XSP + o], acc);
+      ys[kx * XSP + lane] = acc;
+    }
+  }
+  __syncthreads();
+  {  // ColI: [Zr; Zi] (256 x 32) = [[Fr, Fi], [-Fi, Fr]] (256 x 64) [Yr; Yi] (64 x 32)
+    const float* yf = reinterpret_cast<const float*>(ys);
+    auto By = [&](int k, int o) { return yf[2 * ((k & 31) * XSP + o) + (k >> 5)]; };
+    float* zf = reinterpret_cast<float*>(ts);
+    float d[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[h][j][0] = d[h][j][1] = d[h][j][2] = d[h][j][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      FragB bq[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bq[j] = load_b(By, 16 * ks, 8 * j, g, t);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const FragA a = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + h), 16 * ks, g, t);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma3(d[h][j], a, bq[j]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = 16 * (2 * warp + h) + g + (e >> 1) * 8, o = 8 * j + 2 * t + (e & 1);
+          zf[2 * (o * TSP + (row & 127)) + (row >> 7)] = d[h][j][e];
+        }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NIB * FC; i += NTH) {
+    const int iyb = i / FC, c = i % FC;
+    *reinterpret_cast<float4*>(Zout + ((long long)b * NIB + iyb) * BLK + (ky * FC + c) * RB) =
+        *reinterpret_cast<const float4*>(ts + c * TSP + iyb * RB);
+  }
+}
+
+// ------------------------------------------------------------------ backward kernels
+// grad R_l[m][c][o] = sum_b conj(X[m][b][c]) dY[m][b][o], one CTA per mode:
+// real GEMM M = 32 (c), N = 64 (Re / Im of o), K = 64 per chunk of 32 samples.
+__global__ void __launch_bounds__(NTH) fno_dR(const float2* __restrict__ Xst, const float2* __restrict__ dYst, int B,
+                                             float* __restrict__ grad) {
+  __shared__ float2 xs[32 * XSP], gs[32 * XSP];
+  const int m = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int mt = warp & 1, nt0 = (warp >> 1) * 2;
+  float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  const float* xf = reinterpret_cast<const float*>(xs);
+  const float* gf = reinterpret_cast<const float*>(gs);
+  auto A = [&](int c, int k) { return xf[2 * ((k & 31) * XSP + c) + (k >> 5)]; };
+  auto Bg = [&](int k, int n) {
+    const int o = n & 31, bb = k & 31;
+    const float re = gf[2 * (bb * XSP + o)], im = gf[2 * (bb * XSP + o) + 1];
+    return n < 32 ? (k < 32 ? re : im) : (k < 32 ? im : -re);
+  };
+  for (int b0 = 0; b0 < B; b0 += 32) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * FC; i += NTH) {
+      const int bb = b0 + i / FC, c = i % FC;
+      const long long src = ((long long)m * B + bb) * FC + c;
+      xs[(i / FC) * XSP + c] = bb < B ? Xst[src] : make_float2(0.f, 0.f);
+      gs[(i / FC) * XSP + c] = bb < B ? dYst[src] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) mma3(d[j], a, load_b(Bg, 16 * ks, 8 * (nt0 + j), g, t));
+    }
   }
 #pragma unroll
-  for (int i = 0; i < FC; ++i) dvL[(b * FC + i) * FNN + pix] = acc[i];
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = 16 * mt + g + (e >> 1) * 8, n = 8 * (nt0 + j) + 2 * t + (e & 1);
+      grad[((long long)m * FC * FC + c * FC + (n & 31)) * 2 + (n >> 5)] = d[j][e];
+    }
+}
+
+// Layer l backward, persistent over (sample, row block) items:
+//   dv  = dvp + RowI(dU)          (dvp = W_{l+1}^T dpre_{l+1} or the projection's; dU from the column kernel)
+//   dpre = dv * GELU'(pre_l)      (or dv on the last layer)
+//   dvp_out = W_l^T dpre, dT = RowF(dpre),
+//   per-CTA partials of grad W_l = sum_p dpre v_l^T and grad b_l = sum_p dpre.
+constexpr int SM_RBWD = (2 * FC * NPP) * 4 + BLK * 8 + T_ROW * 2 + FC * WP * 2;
+__global__ void __launch_bounds__(NTH, 2) fno_row_bwd(const float* __restrict__ dvp, const float2* __restrict__ dU,
+                                                      const float* __restrict__ pre, const float* __restrict__ v,
+                                                      const __nv_bfloat16* __restrict__ wbf, long long woff,
+                                                      const __nv_bfloat16* __restrict__ tabs, int B, int act,
+                                                      float* __restrict__ dvp_out, float2* __restrict__ dT,
+                                                      float* __restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  float* gs = smem;                                        // [FC][NPP] dv, then dpre
+  float* vs = gs + FC * NPP;                               // [FC][NPP] v_l
+  float2* zs = reinterpret_cast<float2*>(vs + FC * NPP);   // [BLK] dU block, then the dT block
+  __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(zs + BLK);  // [T_ROW]
+  __nv_bfloat16* wt = tb + T_ROW;                          // [FC][WP]: W^T (i, o)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  cta_copy(tb, tabs, T_ROW * 2);
+  load_w(wbf + woff, nullptr, wt);
+  float dw[4] = {0.f, 0.f, 0.f, 0.f};
+  float db = 0.f;
+  const int items = B * NIB;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = it / NIB, iyb = it % NIB, iy0 = iyb * RB;
+    const long long pix0 = (long long)iy0 * FN;
+    const long long gbase = (long long)b * FC * FNN + pix0;
+    load_planar(gs, dvp, b, pix0);
+    load_planar(vs, v, b, pix0);
+    if (dU) cta_copy(zs, dU + ((long long)b * NIB + iyb) * BLK, BLK * 8);
+    cp_wait_all();
+    __syncthreads();
+    if (dU) {
+      row_inverse(zs, tb, gs, true);
+      __syncthreads();
+    }
+    if (act)
+      planar_pass(gs, gbase, [&](float4& x, long long gi) {
+        const float4 p = *reinterpret_cast<const float4*>(pre + gi);
+        x.x *= gelu_grad_f(p.x);
+        x.y *= gelu_grad_f(p.y);
+        x.z *= gelu_grad_f(p.z);
+        x.w *= gelu_grad_f(p.w);
+      });
+    __syncthreads();
+    // dvp_out = W^T dpre: GEMM M = NP, N = FC (i), K = FC (o)
+    pixel_mix([&](int p, int o) { return gs[o * NPP + p]; }, wt,
+              [&](int p, int i, float val) { dvp_out[gbase + (long long)i * FNN + p] = val; });
+    {  // grad W += dpre v^T: GEMM M = FC (o), N = FC (i), K = NP; warp = one 16 x 8 tile
+      auto A = [&](int o, int p) { return gs[o * NPP + p]; };
+      auto Bv = [&](int p, int i) { return vs[i * NPP + p]; };
+      const int mt = warp & 1, nt = warp >> 1;
+#pragma unroll 4
+      for (int ks = 0; ks < NP / 16; ++ks) mma3(dw, load_a(A, 16 * mt, 16 * ks, g, t), load_b(Bv, 16 * ks, 8 * nt, g, t));
+      const int o = threadIdx.x >> 3;
+      for (int p = threadIdx.x & 7; p < NP; p += 8) db += gs[o * NPP + p];
+    }
+    row_forward(gs, tb, zs);
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(dT + ((long long)b * NIB + iyb) * BLK);
+    for (int i = threadIdx.x; i < BLK / 2; i += NTH) dst[i] = reinterpret_cast<float4*>(zs)[i];
+    __syncthreads();
+  }
+  float* pp = part + (long long)blockIdx.x * PART_W;
+  {
+    const int mt = warp & 1, nt = warp >> 1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pp[(16 * mt + g + (e >> 1) * 8) * FC + 8 * nt + 2 * t + (e & 1)] = dw[e];
+  }
+  db += __shfl_xor_sync(0xffffffffu, db, 1);
+  db += __shfl_xor_sync(0xffffffffu, db, 2);
+  db += __shfl_xor_sync(0xffffffffu, db, 4);
+  if ((threadIdx.x & 7) == 0) pp[FC * FC + (threadIdx.x >> 3)] = db;
+}
+
+// Projection backward, persistent over items: recomputes z = P1 v4 + c1 per chunk of 32 hidden
+// units, dz = (P2^T dout) GELU'(z); dvp_out = P1^T dz; per-CTA partials of grad P1, c1, P2, c2.
+constexpr int SM_PBWD = (3 * FC * NPP + 2 * NPP + FH + 2 * FH) * 4 + (FH * WP + FC * P1TP) * 2;
+__global__ void __launch_bounds__(NTH, 1) fno_proj_bwd(const float* __restrict__ v4, const float* __restrict__ dout,
+                                                       const __nv_bfloat16* __restrict__ wbf,
+                                                       const float* __restrict__ pm, int B,
+                                                       float* __restrict__ dvp_out, float* __restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  float* vs = smem;              // [FC][NPP] v4
+  float* zs = vs + FC * NPP;     // [32][NPP] dz of the chunk
+  float* hs = zs + FC * NPP;     // [32][NPP] h of the chunk
+  float* ds = hs + FC * NPP;     // [2][NPP] dout
+  float* c1 = ds + 2 * NPP;      // [FH]
+  float* p2 = c1 + FH;           // [2][FH]
+  __nv_bfloat16* p1 = reinterpret_cast<__nv_bfloat16*>(p2 + 2 * FH);  // [FH][WP] P1[hid][c]
+  __nv_bfloat16* p1t = p1 + FH * WP;                                   // [FC][P1TP] P1^T[c][hid]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  for (int e = threadIdx.x; e < FH * FC; e += NTH) {
+    const __nv_bfloat16 w = wbf[F_P1 + e];
+    p1[(e / FC) * WP + e % FC] = w;
+    p1t[(e % FC) * P1TP + e / FC] = w;
+  }
+  for (int i = threadIdx.x; i < FH; i += NTH) c1[i] = pm[F_C1 + i];
+  for (int i = threadIdx.x; i < 2 * FH; i += NTH) p2[i] = __bfloat162float(wbf[F_P2 + i]);
+  const uint32_t* p132 = reinterpret_cast<const uint32_t*>(p1);
+  const uint32_t* p1t32 = reinterpret_cast<const uint32_t*>(p1t);
+  float ap1[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ap1[q][0] = ap1[q][1] = ap1[q][2] = ap1[q][3] = 0.f;
+  float ac1[4] = {0.f, 0.f, 0.f, 0.f}, ap2[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, ac2 = 0.f;
+  const int items = B * NIB;
+  auto Av = [&](int p, int c) { return vs[c * NPP + p]; };
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = it / NIB, iyb = it % NIB, iy0 = iyb * RB;
+    const long long pix0 = (long long)iy0 * FN;
+    load_planar(vs, v4, b, pix0);
+    for (int o = 0; o < 2; ++o) cta_copy(ds + o * NPP, dout + ((long long)b * 2 + o) * FNN + pix0, NP * 4);
+    cp_wait_all();
+    __syncthreads();
+    {
+      const int o = threadIdx.x >> 7;
+      for (int p = threadIdx.x & 127; p < NP; p += 128) ac2 += ds[o * NPP + p];
+    }
+    FragA av[2][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) av[h][ks] = load_a(Av, 16 * (2 * warp + h), 16 * ks, g, t);
+    float adv[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) adv[h][j][0] = adv[h][j][1] = adv[h][j][2] = adv[h][j][3] = 0.f;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int mt = 2 * warp + h;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          uint32_t b0[2], b1[2];
+          load_b_tab(p132, WP / 2, 0, 32 * q + 8 * nt, g, t, b0);
+          load_b_tab(p132, WP / 2, 16, 32 * q + 8 * nt, g, t, b1);
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+          mma2(d, av[h][0], b0);
+          mma2(d, av[h][1], b1);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int p = 16 * mt + g + (e >> 1) * 8, hl = 8 * nt + 2 * t + (e & 1), hid = 32 * q + hl;
+            const float z = d[e] + c1[hid];
+            const float dh = p2[hid] * ds[p] + p2[FH + hid] * ds[NPP + p];
+            hs[hl * NPP + p] = gelu_f(z);
+            zs[hl * NPP + p] = dh * gelu_grad_f(z);
+          }
+        }
+      }
+      __syncthreads();
+      {  // dv += P1_chunk^T dz: GEMM M = NP, N = FC, K = 32 (B = P1^T rows, pairs along hidden)
+        auto Ad = [&](int p, int hl) { return zs[hl * NPP + p]; };
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int mt = 2 * warp + h;
+          const FragA a0 = load_a(Ad, 16 * mt, 0, g, t), a1 = load_a(Ad, 16 * mt, 16, g, t);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            uint32_t b0[2], b1[2];
+            load_b_tab(p1t32, P1TP / 2, 32 * q, 8 * nt, g, t, b0);
+            load_b_tab(p1t32, P1TP / 2, 32 * q + 16, 8 * nt, g, t, b1);
+            mma2(adv[h][nt], a0, b0);
+            mma2(adv[h][nt], a1, b1);
+          }
+        }
+      }
+      {  // grad P1_chunk += dz v4^T: GEMM M = 32 (hidden), N = FC, K = NP; one tile per warp
+        auto Ad = [&](int hl, int p) { return zs[hl * NPP + p]; };
+        auto Bv = [&](int p, int c) { return vs[c * NPP + p]; };
+        const int mt = warp & 1, nt = warp >> 1;
+#pragma unroll 4
+        for (int ks = 0; ks < NP / 16; ++ks)
+          mma3(ap1[q], load_a(Ad, 16 * mt, 16 * ks, g, t), load_b(Bv, 16 * ks, 8 * nt, g, t));
+        const int hl = threadIdx.x >> 3;
+        for (int p = threadIdx.x & 7; p < NP; p += 8) {
+          ac1[q] += zs[hl * NPP + p];
+          ap2[q][0] += ds[p] * hs[hl * NPP + p];
+          ap2[q][1] += ds[NPP + p] * hs[hl * NPP + p];
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = 16 * (2 * warp + h) + g + (e >> 1) * 8, c = 8 * nt + 2 * t + (e & 1);
+          dvp_out[((long long)b * FC + c) * FNN + pix0 + p] = adv[h][nt][e];
+        }
+  }
+  __shared__ float red2[NTH];
+  float* pp = part + (long long)blockIdx.x * PART_P;
+  {
+    const int mt = warp & 1, nt = warp >> 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        pp[(32 * q + 16 * mt + g + (e >> 1) * 8) * FC + 8 * nt + 2 * t + (e & 1)] = ap1[q][e];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float s = ac1[q], s0 = ap2[q][0], s1 = ap2[q][1];
+#pragma unroll
+    for (int k = 1; k < 8; k <<= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, k);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, k);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, k);
+    }
+    if ((threadIdx.x & 7) == 0) {
+      const int hid = 32 * q + (threadIdx.x >> 3);
+      pp[FH * FC + hid] = s;
+      pp[FH * FC + FH + hid] = s0;
+      pp[FH * FC + 2 * FH + hid] = s1;
+    }
+  }
+  red2[threadIdx.x] = ac2;
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float s = 0.f;
+    for (int i = 0; i < 128; ++i) s += red2[threadIdx.x * 128 + i];
+    pp[FH * FC + 3 * FH + threadIdx.x] = s;
+  }
+}
+
+// Lifting backward, persistent: dv0 = dvp + RowI(dU0); per-CTA partials of
+// grad W0 = sum_p dv0 a^T (features recomputed) and grad b0 = sum_p dv0.
+constexpr int SM_LBWD = (FC * NPP + FIN * NPP) * 4 + ((RB + 2) * FN + NP + BLK) * 8 + T_ROW * 2;
+__global__ void __launch_bounds__(NTH, 2) fno_lift_bwd(const float* __restrict__ dvp, const float2* __restrict__ dU,
+                                                       const float2* __restrict__ f, int fps,
+                                                       const float2* __restrict__ u_in,
+                                                       const __nv_bfloat16* __restrict__ tabs, int B,
+                                                       float* __restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  float* gs = smem;                                        // [FC][NPP]
+  float* as = gs + FC * NPP;                               // [FIN][NPP]
+  float2* us = reinterpret_cast<float2*>(as + FIN * NPP);  // [(RB + 2) FN]
+  float2* fs = us + (RB + 2) * FN;                         // [NP]
+  float2* zs = fs + NP;                                    // [BLK]
+  __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(zs + BLK);  // [T_ROW]
+  __shared__ float red[NTH / 32][4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  cta_copy(tb, tabs, T_ROW * 2);
+  float dw[4] = {0.f, 0.f, 0.f, 0.f};
+  float db = 0.f;
+  const int items = B * NIB;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int b = it / NIB, iyb = it % NIB, iy0 = iyb * RB;
+    load_planar(gs, dvp, b, (long long)iy0 * FN);
+    cta_copy(zs, dU + ((long long)b * NIB + iyb) * BLK, BLK * 8);
+    load_inputs(u_in, f, fps, b, iy0, us, fs);
+    cp_wait_all();
+    __syncthreads();
+    row_inverse(zs, tb, gs, true);
+    features(us, fs, iy0, as);
+    __syncthreads();
+    {  // grad W0 += dv0 a^T: M = FC, N = 8, K = NP split over warp quarters
+      auto A = [&](int c, int p) { return gs[c * NPP + p]; };
+      auto Ba = [&](int p, int k) { return as[k * NPP + p]; };
+      const int mt = warp & 1, kq = warp >> 1;
+#pragma unroll
+      for (int ks = 0; ks < NP / 64; ++ks)
+        mma3(dw, load_a(A, 16 * mt, 64 * kq + 16 * ks, g, t), load_b(Ba, 64 * kq + 16 * ks, 0, g, t));
+      const int c = threadIdx.x >> 3;
+      for (int p = threadIdx.x & 7; p < NP; p += 8) db += gs[c * NPP + p];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) red[warp][e][lane] = dw[e];
+  db += __shfl_xor_sync(0xffffffffu, db, 1);
+  db += __shfl_xor_sync(0xffffffffu, db, 2);
+  db += __shfl_xor_sync(0xffffffffu, db, 4);
+  __syncthreads();
+  float* pp = part + (long long)blockIdx.x * PART_0;
+  if (warp < 2) {  // sum the four K quarters of tile mt = warp in a fixed order
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float s = red[warp][e][lane] + red[warp + 2][e][lane] + red[warp + 4][e][lane] + red[warp + 6][e][lane];
+      pp[(16 * warp + g + (e >> 1) * 8) * FIN + 2 * t + (e & 1)] = s;
+    }
+  }
+  if ((threadIdx.x & 7) == 0) pp[FC * FIN + (threadIdx.x >> 3)] = db;
+}
+
+__global__ void fno_reduce(const float* __restrict__ part, int nparts, int count, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float s = 0.f;
+  for (int p = 0; p < nparts; ++p) s += part[(long long)p * count + i];
+  out[i] = s;
 }
 
 // Per-sample relative L2 loss and its gradient (planar [B][2][FNN]); one CTA per sample.
@@ -493,55 +1021,54 @@ __global__ void __launch_bounds__(256) fno_loss(const float2* __restrict__ out, 
   }
 }
 
-// G[o][i] += sum_p X[b][o][p] Y[b][i][p] over all B * FNN pixels (and gb[o] += sum_p X[o][p]).
-// Each CTA reduces a 1024-pixel chunk in shared tiles of 32 pixels, then adds atomically.
-template <int O, int I>
-__global__ void __launch_bounds__(256) fno_outer(const float* __restrict__ X, const float* __restrict__ Y, int B,
-                                                 float* __restrict__ G, float* __restrict__ gb) {
-  constexpr int TP = 32, CH = 1024;
-  constexpr int PER = (O * I + 255) / 256;
-  __shared__ float Xs[O][TP + 1];
-  __shared__ float Ys[I][TP + 1];
-  const long long p0 = (long long)blockIdx.x * CH;
-  float acc[PER];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
-  float bacc = 0.f;
-  for (int t0 = 0; t0 < CH; t0 += TP) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < (O + I) * TP; e += 256) {
-      const int ch = e / TP, pp = e % TP;
-      const long long p = p0 + t0 + pp;
-      const long long b = p / FNN, pix = p % FNN;
-      if (ch < O)
-        Xs[ch][pp] = (b < B) ? X[(b * O + ch) * FNN + pix] : 0.f;
-      else
-        Ys[ch - O][pp] = (b < B) ? Y[(b * I + (ch - O)) * FNN + pix] : 0.f;
+// FP64 DFT tables as BF16 hi / lo pairs in the fragment layouts described above.
+__device__ double row_entry(int ix, int kyc) {  // E(ix, kyc)
+  double s, c;
+  sincospi(2.0 * (((kyc >> 1) * ix) % FN) / FN, &s, &c);
+  return (kyc & 1) ? -s : c;
+}
+__device__ double2 col_entry(int kx, int iy) {  // F(kx, iy) = exp(-2 pi j kx' iy / 128)
+  const int kv = kx < FM ? kx : kx + FN - FKX;
+  double s, c;
+  sincospi(2.0 * ((kv * iy) % FN) / FN, &s, &c);
+  return make_double2(c, -s);
+}
+__global__ void fno_tables(__nv_bfloat16* __restrict__ tabs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  __nv_bfloat16 *hi, *lo;
+  if (i < T_RF) {  // RowF [kyc][ix]
+    const int kyc = i / RFP, ix = i % RFP;
+    if (ix < FN) v = row_entry(ix, kyc);
+    hi = tabs + i;
+    lo = tabs + T_RF + i;
+  } else if (i < T_RF + T_RI) {  // RowI [ix][kyc]
+    const int j = i - T_RF, ix = j / RIP, kyc = j % RIP;
+    if (kyc < 2 * FM) v = row_entry(ix, kyc);
+    hi = tabs + 2 * T_RF + j;
+    lo = hi + T_RI;
+  } else if (i < T_RF + T_RI + T_CF) {  // ColF [row][k]: [[Fr, -Fi], [Fi, Fr]]
+    const int j = i - T_RF - T_RI, row = j / CFP, k = j % CFP;
+    if (k < 2 * FN) {
+      const double2 F = col_entry(row & 31, k & 127);
+      v = (row < 32) ? ((k < FN) ? F.x : -F.y) : ((k < FN) ? F.y : F.x);
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      if (e < O * I) {
-        const int o = e / I, i = e % I;
-        float s = 0.f;
-#pragma unroll 8
-        for (int pp = 0; pp < TP; ++pp) s += Xs[o][pp] * Ys[i][pp];
-        acc[k] += s;
-      }
+    hi = tabs + T_ROW + j;
+    lo = hi + T_CF;
+  } else if (i < T_RF + T_RI + T_CF + T_CI) {  // ColI [row][k]: [[Fr, Fi], [-Fi, Fr]]
+    const int j = i - T_RF - T_RI - T_CF, row = j / CIP, k = j % CIP;
+    if (k < 2 * FKX) {
+      const double2 F = col_entry(k & 31, row & 127);
+      v = (row < FN) ? ((k < FKX) ? F.x : F.y) : ((k < FKX) ? -F.y : F.x);
     }
-    if (gb && threadIdx.x < O) {
-      float s = 0.f;
-      for (int pp = 0; pp < TP; ++pp) s += Xs[threadIdx.x][pp];
-      bacc += s;
-    }
+    hi = tabs + T_ROW + 2 * T_CF + j;
+    lo = hi + T_CI;
+  } else {
+    return;
   }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + 256 * k;
-    if (e < O * I) atomicAdd(G + e, acc[k]);
-  }
-  if (gb && threadIdx.x < O) atomicAdd(gb + threadIdx.x, bacc);
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+  *hi = h;
+  *lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
 }
 
 __global__ void fno_to_bf16(const float* __restrict__ pm, __nv_bfloat16* __restrict__ wbf, long long n) {
@@ -575,13 +1102,6 @@ __global__ void fno_adam(float* __restrict__ pm, const float* __restrict__ g, fl
   wbf[i] = __float2bfloat16_rn(p);
 }
 
-// x0 = u_in + u_in e (e = demodulated scattered field)
-__global__ void fno_add_incident(const float2* __restrict__ u_in, const float2* __restrict__ e,
-                                 float2* __restrict__ x0, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x0[i] = c_add(u_in[i], c_mul(u_in[i], e[i]));
-}
-
 // Seeded initialisation (SplitMix64 per element): weights uniform in
 // [-1, 1] x (1 / sqrt(fan_in)) (spectral weights x 1 / C), biases 0.
 __device__ __forceinline__ float init_uniform(unsigned long long seed, long long i) {
@@ -600,8 +1120,7 @@ __global__ void fno_init(float* __restrict__ pm, long long n, unsigned long long
   else if (i >= F_P1 && i < F_C1) scale = 0.17677670f;  // 1/sqrt(32)
   else if (i >= F_P2 && i < F_C2) scale = 0.08838835f;  // 1/sqrt(128)
   else if (i >= F_LAYERS && i < F_P1) {
-    const long long l = (i - F_LAYERS) / F_LAYER, off = (i - F_LAYERS) % F_LAYER;
-    (void)l;
+    const long long off = (i - F_LAYERS) % F_LAYER;
     if (off < (long long)FMODES * FC * FC * 2) scale = 1.f / FC;
     else if (off < (long long)FMODES * FC * FC * 2 + FC * FC) scale = 0.17677670f;
   }
@@ -614,15 +1133,16 @@ using namespace cisor;
 
 struct cisor_fno {
   int max_batch;
+  int grid_bwd;  // CTAs of the persistent backward kernels
   cudaStream_t user_stream, stream;
   cudaEvent_t ev_a, ev_b;
-  float *pm, *grad, *m1, *m2;
+  float *pm, *grad, *m1, *m2, *part;
   __nv_bfloat16* wbf;
-  float2* twst;
+  __nv_bfloat16* tabs;  // [T_ALL] DFT tables (BF16 hi / lo)
   long long adam_t;
   // activations [max_batch, ...]
-  float *feat, *v[FL + 1], *pre[FL], *z, *h, *dout, *dvA, *dvB, *dpre, *loss;
-  float2 *X[FL], *Y, *dY, *dX, *out, *fbuf, *ubuf, *tbuf, *usc;
+  float *v[FL + 1], *pre[FL], *dout, *dvA, *dvB, *loss;
+  float2 *Xst[FL], *dYst, *T1, *Zb, *out, *fbuf, *ubuf, *tbuf, *usc;
   float* h_loss;
 };
 
@@ -641,64 +1161,75 @@ cisor_status fno_leave(cisor_fno* F) {
 
 unsigned grid_of(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// forward pass on F->fbuf / F->ubuf (f_per_sample as given), leaves F->out;
-// store keeps the projection's z and h for a backward pass
-cisor_status fno_forward_core(cisor_fno* F, int fps, int B, int store = 1) {
-  cudaStream_t s = F->stream;
-  const long long BP = (long long)B * FNN;
-  fno_features_lift<<<grid_of(BP, 256), 256, 0, s>>>(F->fbuf, fps, F->ubuf, F->wbf, F->pm, B, F->feat, F->v[0]);
-  CISOR_CUDA(cudaGetLastError());
-  for (int l = 0; l < FL; ++l) {
-    fno_analysis<<<B * FC, 256, 0, s>>>(F->v[l], F->X[l], F->twst, 1.f, 0);
-    CISOR_CUDA(cudaGetLastError());
-    fno_mix_fwd<<<FMODES, 256, 0, s>>>(F->X[l], F->wbf, f_R(l), B, F->Y);
-    CISOR_CUDA(cudaGetLastError());
-    fno_synthesis<<<B * FC, 256, 0, s>>>(F->Y, F->pre[l], F->twst, 1.f / FNN, 1, 0);
-    CISOR_CUDA(cudaGetLastError());
-    fno_pointwise_fwd<<<grid_of(BP, 128), 128, 0, s>>>(F->pre[l], F->v[l], F->wbf, F->pm, f_W(l), f_B(l), B,
-                                                       l < FL - 1, F->v[l + 1]);
-    CISOR_CUDA(cudaGetLastError());
-  }
-  if (store)
-    fno_proj_fwd_tc<1><<<grid_of(BP, 64), 128, 0, s>>>(F->v[FL], F->wbf, F->pm, B, F->z, F->h, F->out);
-  else
-    fno_proj_fwd_tc<0><<<grid_of(BP, 64), 128, 0, s>>>(F->v[FL], F->wbf, F->pm, B, F->z, F->h, F->out);
-  CISOR_CUDA(cudaGetLastError());
+cisor_status fno_kernel_attrs() {
+  CISOR_CUDA(cudaFuncSetAttribute(fno_lift_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_LIFT));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_row_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_row_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_col<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_col<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_row_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_RBWD));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_proj_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_PBWD));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_lift_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_LBWD));
   return CISOR_OK;
 }
 
-// loss and gradients (into F->grad) for targets in F->tbuf
-cisor_status fno_backward_core(cisor_fno* F, int B) {
+// Forward pass on F->fbuf / F->ubuf (f_per_sample as given); train keeps pre, v_4
+// and the spectra X for the backward pass.  out (may be null) receives e; x0 (may be
+// null) receives the warm start u_in (1 + e) for u_in = xin.
+cisor_status fno_forward_core(cisor_fno* F, int fps, int B, int train, const float2* xin, float2* x0) {
   cudaStream_t s = F->stream;
-  const long long BP = (long long)B * FNN;
-  const unsigned gch = grid_of(BP, 1024);
-  CISOR_CUDA(cudaMemsetAsync(F->grad, 0, sizeof(float) * F_TOTAL, s));
+  const dim3 grow(NIB, B), gcol(FM, B);
+  const int gper = (int)((long long)B * NIB < F->grid_bwd ? (long long)B * NIB : F->grid_bwd);
+  fno_lift_fwd<<<grow, NTH, SM_LIFT, s>>>(F->fbuf, fps, xin, F->wbf, F->pm, F->tabs, F->v[0], F->T1);
+  CISOR_CUDA(cudaGetLastError());
+  for (int l = 0; l < FL; ++l) {
+    fno_col<0><<<gcol, NTH, SM_COL, s>>>(F->T1, F->tabs, F->wbf, f_R(l), B, train ? F->Xst[l] : nullptr, F->Zb);
+    CISOR_CUDA(cudaGetLastError());
+    const int last = l == FL - 1;
+    float* pre = train ? F->pre[l] : nullptr;
+    if (!last) {
+      fno_row_fwd<0><<<gper, NTH, SM_ROW, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 1, B, pre,
+                                              F->v[l + 1], F->T1, nullptr, nullptr, nullptr);
+    } else {
+      fno_row_fwd<1><<<gper, NTH, SM_ROW, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 0, B, pre,
+                                              train ? F->v[FL] : nullptr, nullptr, F->out, xin, x0);
+    }
+    CISOR_CUDA(cudaGetLastError());
+  }
+  return CISOR_OK;
+}
+
+// loss and gradients (into F->grad) for targets in F->tbuf, after a training forward pass
+cisor_status fno_backward_core(cisor_fno* F, int fps, int B) {
+  cudaStream_t s = F->stream;
+  const int G = F->grid_bwd;
+  const int Gi = (int)((long long)B * NIB < G ? (long long)B * NIB : G);
+  const dim3 gcol(FM, B);
   fno_loss<<<B, 256, 0, s>>>(F->out, F->tbuf, B, F->dout, F->loss);
   CISOR_CUDA(cudaGetLastError());
-  fno_outer<2, FH><<<gch, 256, 0, s>>>(F->dout, F->h, B, F->grad + F_P2, F->grad + F_C2);
+  fno_proj_bwd<<<Gi, NTH, SM_PBWD, s>>>(F->v[FL], F->dout, F->wbf, F->pm, B, F->dvA, F->part);
   CISOR_CUDA(cudaGetLastError());
-  fno_proj_bwd<<<grid_of(BP, 128), 128, 0, s>>>(F->dout, F->z, F->wbf, B, F->dvA);
-  CISOR_CUDA(cudaGetLastError());
-  fno_outer<FH, FC><<<gch, 256, 0, s>>>(F->z, F->v[FL], B, F->grad + F_P1, F->grad + F_C1);
+  fno_reduce<<<grid_of(PART_P, 256), 256, 0, s>>>(F->part, Gi, PART_P, F->grad + F_P1);
   CISOR_CUDA(cudaGetLastError());
   float* dv = F->dvA;
   float* dvn = F->dvB;
   for (int l = FL - 1; l >= 0; --l) {
-    fno_pointwise_bwd<<<grid_of(BP, 128), 128, 0, s>>>(dv, F->pre[l], F->wbf, f_W(l), B, l < FL - 1, F->dpre, dvn);
+    fno_row_bwd<<<Gi, NTH, SM_RBWD, s>>>(dv, l == FL - 1 ? nullptr : F->Zb, F->pre[l], F->v[l], F->wbf, f_W(l),
+                                         F->tabs, B, l < FL - 1, dvn, F->T1, F->part);
     CISOR_CUDA(cudaGetLastError());
-    fno_outer<FC, FC><<<gch, 256, 0, s>>>(F->dpre, F->v[l], B, F->grad + f_W(l), F->grad + f_B(l));
+    fno_reduce<<<grid_of(PART_W, 256), 256, 0, s>>>(F->part, Gi, PART_W, F->grad + f_W(l));
     CISOR_CUDA(cudaGetLastError());
-    fno_analysis<<<B * FC, 256, 0, s>>>(F->dpre, F->dY, F->twst, 1.f / FNN, 1);
+    fno_col<1><<<gcol, NTH, SM_COL, s>>>(F->T1, F->tabs, F->wbf, f_R(l), B, F->dYst, F->Zb);
     CISOR_CUDA(cudaGetLastError());
-    fno_mix_bwd<<<FMODES, 256, 0, s>>>(F->X[l], F->dY, F->wbf, f_R(l), B, F->dX, F->grad);
+    fno_dR<<<FMODES, NTH, 0, s>>>(F->Xst[l], F->dYst, B, F->grad + f_R(l));
     CISOR_CUDA(cudaGetLastError());
-    fno_synthesis<<<B * FC, 256, 0, s>>>(F->dX, dvn, F->twst, 1.f, 0, 1);
-    CISOR_CUDA(cudaGetLastError());
-    float* t = dv;
+    float* tmp = dv;
     dv = dvn;
-    dvn = t;
+    dvn = tmp;
   }
-  fno_outer<FC, FIN><<<gch, 256, 0, s>>>(dv, F->feat, B, F->grad + F_W0, F->grad + F_B0);
+  fno_lift_bwd<<<Gi, NTH, SM_LBWD, s>>>(dv, F->Zb, F->fbuf, fps, F->ubuf, F->tabs, B, F->part);
+  CISOR_CUDA(cudaGetLastError());
+  fno_reduce<<<grid_of(PART_0, 256), 256, 0, s>>>(F->part, Gi, PART_0, F->grad + F_W0);
   CISOR_CUDA(cudaGetLastError());
   return CISOR_OK;
 }
@@ -731,15 +1262,15 @@ cisor_status mean_loss(cisor_fno* F, int B, double* loss) {
 void fno_free(cisor_fno* F) {
   if (!F) return;
   if (F->stream) cudaStreamSynchronize(F->stream);
-  void* d[] = {F->pm, F->grad, F->m1, F->m2, F->wbf, F->twst, F->feat, F->z, F->h, F->dout, F->dvA, F->dvB,
-               F->dpre, F->loss, F->Y, F->dY, F->dX, F->out, F->fbuf, F->ubuf, F->tbuf, F->usc};
+  void* d[] = {F->pm,  F->grad, F->m1,   F->m2,  F->part, F->wbf,  F->tabs, F->dout, F->dvA,
+               F->dvB, F->loss, F->dYst, F->T1,  F->Zb,   F->out,  F->fbuf, F->ubuf, F->tbuf, F->usc};
   for (void* p : d)
     if (p) cudaFree(p);
   for (int l = 0; l <= FL; ++l)
     if (F->v[l]) cudaFree(F->v[l]);
   for (int l = 0; l < FL; ++l) {
     if (F->pre[l]) cudaFree(F->pre[l]);
-    if (F->X[l]) cudaFree(F->X[l]);
+    if (F->Xst[l]) cudaFree(F->Xst[l]);
   }
   if (F->h_loss) cudaFreeHost(F->h_loss);
   if (F->ev_a) cudaEventDestroy(F->ev_a);
@@ -770,26 +1301,41 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
     fno_free(F);
     return st;
   };
-  cudaError_t e = cudaStreamCreateWithFlags(&F->stream, cudaStreamNonBlocking);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(e, "device query");
+  F->grid_bwd = 2 * sms;
+  e = cudaStreamCreateWithFlags(&F->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_a, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_b, cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(e, "FNO stream/events");
   const size_t act = sizeof(float) * (size_t)max_batch * FC * FNN;
-  const size_t hid = sizeof(float) * (size_t)max_batch * FH * FNN;
+  const size_t spec = sizeof(float2) * (size_t)max_batch * NIB * BLK;
   const size_t md = sizeof(float2) * (size_t)max_batch * FC * FMODES;
   const size_t fld = sizeof(float2) * (size_t)max_batch * FNN;
   struct A {
     void** p;
     size_t n;
-  } allocs[] = {{(void**)&F->pm, sizeof(float) * F_TOTAL}, {(void**)&F->grad, sizeof(float) * F_TOTAL},
-                {(void**)&F->m1, sizeof(float) * F_TOTAL},  {(void**)&F->m2, sizeof(float) * F_TOTAL},
-                {(void**)&F->wbf, sizeof(__nv_bfloat16) * F_TOTAL}, {(void**)&F->twst, sizeof(float2) * 2 * TW_STRIDE},
-                {(void**)&F->feat, sizeof(float) * (size_t)max_batch * FIN * FNN}, {(void**)&F->z, hid},
-                {(void**)&F->h, hid}, {(void**)&F->dout, sizeof(float) * (size_t)max_batch * 2 * FNN},
-                {(void**)&F->dvA, act}, {(void**)&F->dvB, act}, {(void**)&F->dpre, act},
-                {(void**)&F->loss, sizeof(float) * max_batch}, {(void**)&F->Y, md}, {(void**)&F->dY, md},
-                {(void**)&F->dX, md}, {(void**)&F->out, fld}, {(void**)&F->fbuf, fld}, {(void**)&F->ubuf, fld},
-                {(void**)&F->tbuf, fld}, {(void**)&F->usc, fld}};
+  } allocs[] = {{(void**)&F->pm, sizeof(float) * F_TOTAL},
+                {(void**)&F->grad, sizeof(float) * F_TOTAL},
+                {(void**)&F->m1, sizeof(float) * F_TOTAL},
+                {(void**)&F->m2, sizeof(float) * F_TOTAL},
+                {(void**)&F->part, sizeof(float) * (size_t)F->grid_bwd * PART_MAX},
+                {(void**)&F->wbf, sizeof(__nv_bfloat16) * F_TOTAL},
+                {(void**)&F->tabs, sizeof(__nv_bfloat16) * T_ALL},
+                {(void**)&F->dout, sizeof(float) * (size_t)max_batch * 2 * FNN},
+                {(void**)&F->dvA, act},
+                {(void**)&F->dvB, act},
+                {(void**)&F->loss, sizeof(float) * max_batch},
+                {(void**)&F->dYst, md},
+                {(void**)&F->T1, spec},
+                {(void**)&F->Zb, spec},
+                {(void**)&F->out, fld},
+                {(void**)&F->fbuf, fld},
+                {(void**)&F->ubuf, fld},
+                {(void**)&F->tbuf, fld},
+                {(void**)&F->usc, fld}};
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return fail(e, "FNO cudaMalloc");
@@ -797,26 +1343,23 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
   for (int l = 0; l <= FL && e == cudaSuccess; ++l) e = cudaMalloc((void**)&F->v[l], act);
   for (int l = 0; l < FL && e == cudaSuccess; ++l) {
     e = cudaMalloc((void**)&F->pre[l], act);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&F->X[l], md);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&F->Xst[l], md);
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_loss, sizeof(float) * max_batch);
   if (e != cudaSuccess) return fail(e, "FNO cudaMalloc");
-  fno_init<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F_TOTAL, seed);
-  fno_to_bf16<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F->wbf, F_TOTAL);
-  e = cudaMemsetAsync(F->m1, 0, sizeof(float) * F_TOTAL, F->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(F->m2, 0, sizeof(float) * F_TOTAL, F->stream);
-  if (e != cudaSuccess) return fail(e, "FNO init");
-  cisor_ctx tw{};
-  tw.P = FN;
-  tw.twst = F->twst;
-  tw.stream = F->stream;
-  cisor_status st = make_stage_twiddles(&tw);
+  cisor_status st = fno_kernel_attrs();
   if (st != CISOR_OK) {
     fno_free(F);
     return st;
   }
-  e = cudaStreamSynchronize(F->stream);
-  if (e != cudaSuccess) return fail(e, "FNO init sync");
+  fno_init<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F_TOTAL, seed);
+  fno_to_bf16<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F->wbf, F_TOTAL);
+  fno_tables<<<grid_of(T_RF + T_RI + T_CF + T_CI, 256), 256, 0, F->stream>>>(F->tabs);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->m1, 0, sizeof(float) * F_TOTAL, F->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->m2, 0, sizeof(float) * F_TOTAL, F->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(F->stream);
+  if (e != cudaSuccess) return fail(e, "FNO init");
   *out = F;
   return CISOR_OK;
 }
@@ -876,7 +1419,7 @@ cisor_status cisor_fno_forward(cisor_fno* F, const void* f, int f_per_sample, co
   if (bad_batch(F, B)) return CISOR_ERR_INVALID_ARG;
   CISOR_TRY(fno_enter(F));
   CISOR_TRY(stage_inputs(F, f, f_per_sample, u_in, nullptr, B));
-  CISOR_TRY(fno_forward_core(F, f_per_sample, B, 0));
+  CISOR_TRY(fno_forward_core(F, f_per_sample, B, 0, F->ubuf, nullptr));
   CISOR_CUDA(cudaMemcpyAsync(u_sc_out, F->out, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
   CISOR_CUDA(cudaStreamSynchronize(F->stream));
   return fno_leave(F);
@@ -891,8 +1434,8 @@ cisor_status cisor_fno_loss_grad(cisor_fno* F, const void* f, int f_per_sample, 
   if (bad_batch(F, B)) return CISOR_ERR_INVALID_ARG;
   CISOR_TRY(fno_enter(F));
   CISOR_TRY(stage_inputs(F, f, f_per_sample, u_in, target, B));
-  CISOR_TRY(fno_forward_core(F, f_per_sample, B));
-  CISOR_TRY(fno_backward_core(F, B));
+  CISOR_TRY(fno_forward_core(F, f_per_sample, B, 1, F->ubuf, nullptr));
+  CISOR_TRY(fno_backward_core(F, f_per_sample, B));
   if (grad_out)
     CISOR_CUDA(cudaMemcpyAsync(grad_out, F->grad, sizeof(float) * F_TOTAL, cudaMemcpyDefault, F->stream));
   CISOR_TRY(mean_loss(F, B, loss));
@@ -908,8 +1451,8 @@ cisor_status cisor_fno_train_step(cisor_fno* F, const void* f, int f_per_sample,
   if (bad_batch(F, B)) return CISOR_ERR_INVALID_ARG;
   CISOR_TRY(fno_enter(F));
   CISOR_TRY(stage_inputs(F, f, f_per_sample, u_in, target, B));
-  CISOR_TRY(fno_forward_core(F, f_per_sample, B));
-  CISOR_TRY(fno_backward_core(F, B));
+  CISOR_TRY(fno_forward_core(F, f_per_sample, B, 1, F->ubuf, nullptr));
+  CISOR_TRY(fno_backward_core(F, f_per_sample, B));
   F->adam_t += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)F->adam_t), c2 = 1.f - powf(b2, (float)F->adam_t);
@@ -925,17 +1468,16 @@ cisor_status cisor_fno_warm_start(cisor_fno* F, cisor_ctx* c, const void* f, voi
     set_error("cisor_fno_warm_start: NULL argument");
     return CISOR_ERR_INVALID_ARG;
   }
-  if (c->dim != 2 || c->n != FN || c->T > F->max_batch) {
-    set_error("cisor_fno_warm_start: the network is for 128 x 128 grids and at most %d transmitters", F->max_batch);
+  if (c->dim != 2 || c->n != FN || c->ncomp != 1 || c->T > F->max_batch) {
+    set_error("cisor_fno_warm_start: the network is for scalar 128 x 128 grids and at most %d transmitters",
+              F->max_batch);
     return CISOR_ERR_INVALID_ARG;
   }
   const int B = c->T;
   CISOR_TRY(fno_enter(F));
   CISOR_CUDA(cudaMemcpyAsync(F->fbuf, f, sizeof(float2) * FNN, cudaMemcpyDefault, F->stream));
-  CISOR_CUDA(cudaMemcpyAsync(F->ubuf, c->u_in, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDeviceToDevice, F->stream));
-  CISOR_TRY(fno_forward_core(F, 0, B, 0));
-  fno_add_incident<<<grid_of((long long)B * FNN, 256), 256, 0, F->stream>>>(F->ubuf, F->out, F->usc, (long long)B * FNN);
-  CISOR_CUDA(cudaGetLastError());
+  CISOR_CUDA(cudaStreamWaitEvent(F->stream, c->ev_b, 0));  // the context's incident fields are ready
+  CISOR_TRY(fno_forward_core(F, 0, B, 0, c->u_in, F->usc));
   CISOR_CUDA(cudaMemcpyAsync(x0_out, F->usc, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
   CISOR_CUDA(cudaStreamSynchronize(F->stream));
   return fno_leave(F);

@@ -375,6 +375,113 @@ static cisor_status get_graph(cisor_ctx* c, int adjoint, float2* x, int ntx, cud
   return CISOR_OK;
 }
 
+// ---------------------------------------------------------------- whole-solve graphs
+// A solve's iterations run as ONE graph launch: a WHILE conditional node
+// whose body is a chunk of BiCGSTAB iterations (of every problem, forked to
+// their streams) followed by loop_cond_kernel, which keeps the loop going
+// while any transmitter of any problem is active and the body has run fewer
+// than ceil(max_iter / chunk) + 2 times (so the loop always ends, whatever
+// the flags).  The host only waits for the graph, not for every chunk.
+__global__ void loop_cond_kernel(const cisor_loop_item* __restrict__ items, int nitems,
+                                 const double* __restrict__ params, int chunk, int* __restrict__ count,
+                                 cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int a = 0;
+  for (int p = 0; p < nitems; ++p)
+    for (int t = threadIdx.x; t < items[p].ntx; t += blockDim.x) a |= items[p].active[t];
+  if (a) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int cap = (int)(params[1] / chunk) + 2;
+    const int k = *count + 1;
+    *count = k;
+    cudaGraphSetConditional(h, (any && k < cap) ? 1u : 0u);
+  }
+}
+
+// Builds a graph [WHILE { body ; loop_cond_kernel }]: `body` enqueues the
+// iterations on `st` (forking to other streams and joining back is allowed).
+template <class Body>
+static cudaError_t build_while_graph(cudaStream_t st, Body body, const cisor_loop_item* items, int nitems,
+                                     const double* params, int chunk, int* count, cudaGraphExec_t* out,
+                                     cisor_status* body_status) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    *body_status = body();
+    loop_cond_kernel<<<1, 256, 0, st>>>(items, nitems, params, chunk, count, h);
+    cudaError_t el = cudaGetLastError();
+    cudaGraph_t cap = nullptr;
+    e = cudaStreamEndCapture(st, &cap);
+    if (e == cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess && *body_status == CISOR_OK) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// The whole-solve graph of one context (built on first use, rebuilt when x or
+// the transmitter count changes); false when the WHILE graph cannot be built
+// here (the caller then runs the host-driven chunk loop).
+static cisor_status get_while_graph(cisor_ctx* c, int adjoint, float2* x, int ntx, cudaGraphExec_t* out, bool* ok) {
+  *ok = false;
+  if (!c->use_while) return CISOR_OK;
+  if (c->wgraph[adjoint] && c->wgraph_ntx[adjoint] == ntx && c->wgraph_x[adjoint] == x) {
+    *out = c->wgraph[adjoint];
+    *ok = true;
+    return CISOR_OK;
+  }
+  if (c->wgraph[adjoint]) {
+    cudaGraphExecDestroy(c->wgraph[adjoint]);
+    c->wgraph[adjoint] = nullptr;
+  }
+  if (!c->loop_item) {
+    CISOR_CUDA(cudaMalloc((void**)&c->loop_item, sizeof(cisor_loop_item)));
+    CISOR_CUDA(cudaMalloc((void**)&c->loop_count, sizeof(int)));
+    CISOR_CUDA(cudaMallocHost((void**)&c->h_loop_count, sizeof(int)));
+  }
+  const cisor_loop_item it{c->active, ntx};
+  CISOR_CUDA(cudaMemcpyAsync(c->loop_item, &it, sizeof(it), cudaMemcpyHostToDevice, c->stream));
+  CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  const long long l0 = c->launches;
+  cisor_status bs = CISOR_OK;
+  auto body = [&]() {
+    cisor_status s2 = CISOR_OK;
+    for (int i = 0; i < c->graph_chunk && s2 == CISOR_OK; ++i) s2 = enqueue_iteration(c, adjoint, x, ntx);
+    return s2;
+  };
+  cudaError_t e = build_while_graph(c->stream, body, c->loop_item, 1, c->sparams, c->graph_chunk, c->loop_count,
+                                    &c->wgraph[adjoint], &bs);
+  c->graph_kernels[adjoint] = c->launches - l0 + 1;  // captured per body execution (+ the condition)
+  c->launches = l0;
+  if (bs != CISOR_OK) return bs;
+  if (e != cudaSuccess) {  // conditional graphs unavailable: keep the host-driven loop
+    cudaGetLastError();
+    c->wgraph[adjoint] = nullptr;
+    c->use_while = 0;
+    return CISOR_OK;
+  }
+  c->wgraph_ntx[adjoint] = ntx;
+  c->wgraph_x[adjoint] = x;
+  *out = c->wgraph[adjoint];
+  *ok = true;
+  return CISOR_OK;
+}
+
 static cisor_status read_active(cisor_ctx* c, int ntx, int* n_active) {
   CISOR_CUDA(cudaMemcpyAsync(c->h_active, c->active, sizeof(int) * ntx, cudaMemcpyDeviceToHost, c->stream));
   CISOR_CUDA(cudaStreamSynchronize(c->stream));
@@ -448,12 +555,22 @@ cisor_status solve_batch(cisor_ctx* c, int adjoint, const float2* f, const float
   cudaGraphExec_t ge = nullptr;
   int done = 0;
   for (int restart = 0; restart < 6 && nact > 0; ++restart) {
-    CISOR_TRY(get_graph(c, adjoint, x, ntx, &ge));
-    while (nact > 0 && done < max_iter + c->graph_chunk) {
+    bool whole = false;
+    CISOR_TRY(get_while_graph(c, adjoint, x, ntx, &ge, &whole));
+    if (whole) {  // all chunks in one launch; the device decides when to stop
+      CISOR_CUDA(cudaMemsetAsync(c->loop_count, 0, sizeof(int), c->stream));
       CISOR_CUDA(cudaGraphLaunch(ge, c->stream));
-      c->launches += c->graph_kernels[adjoint];
-      done += c->graph_chunk;
-      CISOR_TRY(read_active(c, ntx, &nact));
+      CISOR_CUDA(cudaMemcpyAsync(c->h_loop_count, c->loop_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CISOR_CUDA(cudaStreamSynchronize(c->stream));
+      c->launches += c->graph_kernels[adjoint] * (long long)c->h_loop_count[0];
+    } else {
+      CISOR_TRY(get_graph(c, adjoint, x, ntx, &ge));
+      while (nact > 0 && done < max_iter + c->graph_chunk) {
+        CISOR_CUDA(cudaGraphLaunch(ge, c->stream));
+        c->launches += c->graph_kernels[adjoint];
+        done += c->graph_chunk;
+        CISOR_TRY(read_active(c, ntx, &nact));
+      }
     }
     CISOR_TRY(true_residual(c, adjoint, b, x, ntx));
     CISOR_TRY(read_active(c, ntx, &nact));
@@ -484,11 +601,8 @@ cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2
   };
   int nact = 0;
   CISOR_TRY(count(&nact));
-  if (nact > 0 && !ms.graph[adjoint]) {
-    std::vector<long long> l0(np);
-    for (int i = 0; i < np; ++i) l0[i] = cs[i]->launches;
-    cudaGraph_t g = nullptr;
-    CISOR_CUDA(cudaStreamBeginCapture(ms.main, cudaStreamCaptureModeThreadLocal));
+  // the forked chunk of iterations of every problem (captured into either kind of graph)
+  auto fork_body = [&]() -> cisor_status {
     cisor_status s = CISOR_OK;
     cudaError_t e = cudaEventRecord(ms.fork, ms.main);
     for (int i = 0; i < np && s == CISOR_OK && e == cudaSuccess; ++i) {
@@ -498,6 +612,49 @@ cisor_status solve_multi(cisor_ctx* const* cs, int np, int adjoint, const float2
       if (e == cudaSuccess) e = cudaEventRecord(ms.join[i], cs[i]->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ms.main, ms.join[i], 0);
     }
+    if (s == CISOR_OK && e != cudaSuccess) return cuda_fail(e, "batch graph fork", __FILE__, __LINE__);
+    return s;
+  };
+  if (nact > 0 && ms.use_while && !ms.wgraph[adjoint]) {
+    std::vector<cisor_loop_item> items(np);
+    for (int i = 0; i < np; ++i) items[i] = cisor_loop_item{cs[i]->active, cs[i]->T};
+    CISOR_CUDA(cudaMemcpyAsync(ms.items, items.data(), sizeof(cisor_loop_item) * np, cudaMemcpyHostToDevice, ms.main));
+    CISOR_CUDA(cudaStreamSynchronize(ms.main));
+    std::vector<long long> l0(np);
+    for (int i = 0; i < np; ++i) l0[i] = cs[i]->launches;
+    cisor_status bs = CISOR_OK;
+    cudaError_t e = build_while_graph(ms.main, fork_body, ms.items, np, cs[0]->sparams, cs[0]->graph_chunk,
+                                      ms.loop_count, &ms.wgraph[adjoint], &bs);
+    for (int i = 0; i < np; ++i) {
+      ms.kernels[adjoint][i] = cs[i]->launches - l0[i];
+      cs[i]->launches = l0[i];
+    }
+    if (bs != CISOR_OK) return bs;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ms.wgraph[adjoint] = nullptr;
+      ms.use_while = 0;
+    }
+  }
+  if (nact > 0 && ms.use_while && ms.wgraph[adjoint]) {
+    for (int restart = 0; restart < 6 && nact > 0; ++restart) {
+      CISOR_CUDA(cudaMemsetAsync(ms.loop_count, 0, sizeof(int), ms.main));
+      CISOR_CUDA(cudaGraphLaunch(ms.wgraph[adjoint], ms.main));
+      CISOR_CUDA(cudaMemcpyAsync(ms.h_loop_count, ms.loop_count, sizeof(int), cudaMemcpyDeviceToHost, ms.main));
+      CISOR_CUDA(cudaStreamSynchronize(ms.main));
+      for (int i = 0; i < np; ++i) cs[i]->launches += ms.kernels[adjoint][i] * (long long)ms.h_loop_count[0];
+      for (int i = 0; i < np; ++i) CISOR_TRY(true_residual(cs[i], adjoint, b[i], xof(cs[i]), cs[i]->T));
+      CISOR_TRY(count(&nact));
+    }
+    nact = 0;  // the stats below report any transmitter still above tol
+  }
+  if (nact > 0 && !ms.graph[adjoint]) {
+    std::vector<long long> l0(np);
+    for (int i = 0; i < np; ++i) l0[i] = cs[i]->launches;
+    cudaGraph_t g = nullptr;
+    CISOR_CUDA(cudaStreamBeginCapture(ms.main, cudaStreamCaptureModeThreadLocal));
+    cisor_status s = fork_body();
+    cudaError_t e = cudaSuccess;
     cudaError_t e2 = cudaStreamEndCapture(ms.main, &g);
     for (int i = 0; i < np; ++i) {
       ms.kernels[adjoint][i] = cs[i]->launches - l0[i];

@@ -1,6 +1,7 @@
-"""Problems of uneven size in one batch (one CUDA-graph launch per iteration chunk)
-against the same problems solved one context at a time, and against the oracle;
-the autotuner's choice leaves results unchanged."""
+"""Problems of uneven size in one batch (every problem's whole solve in one CUDA-graph
+launch with a device-side loop) against the same problems solved one context at a
+time and, problem by problem, against the FP64 oracle; the autotuner's choice
+leaves results unchanged."""
 import numpy as np
 import pytest
 
@@ -51,11 +52,14 @@ def test_batch_forward_and_grad_match_single_contexts():
     for i in range(len(SIZES)):
         assert abs(Ds[i] - gs[i][0]) / gs[i][0] < 1e-5
         assert _rel(grads[i], gs[i][1]) < 1e-4
-    # oracle fields of the first problem
-    g = geoms[0]
-    prob = model.Problem(g["n"], g["delta"], g["tx_angles"], g["rx_pos"], P=batch.problems[0].P)
-    ref, _, _ = solve.solve_fields(prob, fs[0].astype(np.complex128), prob.u_in, tol=1e-12)
-    assert _rel(us[0], ref) < 1e-4
+    # every problem's fields and gradient against the FP64 oracle
+    for i, g in enumerate(geoms):
+        prob = model.Problem(g["n"], g["delta"], g["tx_angles"], g["rx_pos"], P=batch.problems[i].P)
+        ref, _, _ = solve.solve_fields(prob, fs[i].astype(np.complex128), prob.u_in, tol=1e-12)
+        assert _rel(us[i], ref) < 1e-4, i
+        D_ref, g_ref = ograd.data_and_grad(prob, fs[i].astype(np.complex128), ys[i].astype(np.complex128), tol=1e-12)
+        assert abs(Ds[i] - D_ref) / D_ref < 1e-4, i
+        assert _rel(grads[i], g_ref) < 5e-4, i
     batch.close()
 
 

@@ -89,3 +89,86 @@ def test_sharded_step_with_identity_reduce_is_step():
     # D sums per-block partials with double atomics, so only its rounding may differ
     assert rel(fb.cpu().numpy(), fa.cpu().numpy()) < 1e-6 and rel(sb.cpu().numpy(), sa.cpu().numpy()) < 1e-6
     assert abs(sta.D - stb.D) <= 1e-12 * sta.D
+
+
+def _shard_rank(rank, world, port, y, s0, gamma, q):
+    """One rank of the two-process test: its own CUDA context (cuda:0) on its transmitter block, the
+    gradient all-reduced by gloo through host memory, cisor_step_update on the summed gradient."""
+    import os
+
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        cfg, f_true, angles, rx = synth.make_inputs("c1")
+        a, b = tx_split(cfg["T"], world, rank)
+        ctx = cisor.Cisor(cfg["n"], cfg["delta"], angles[a:b], rx)
+        dev = torch.device("cuda", 0)
+
+        def host_reduce(g, D):
+            gh = torch.view_as_real(g).cpu()
+            dist.all_reduce(gh)
+            g.copy_(torch.view_as_complex(gh).to(dev))
+            d = torch.tensor([float(D)], dtype=torch.float64)
+            dist.all_reduce(d)
+            return float(d.item())
+
+        f = torch.from_numpy(s0).to(dev)
+        s = torch.from_numpy(s0).to(dev)
+        st = ctx.new_state(f, s, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0)
+        g = torch.empty_like(s)
+        y_loc = torch.from_numpy(y[a:b]).to(dev)
+        Ds = []
+        for _ in range(3):
+            sharded_step(ctx, st, s, y_loc, g, reduce=host_reduce, tol=1e-6, max_iter=3000, x0_mode=2)
+            Ds.append(st.D)
+        torch.cuda.synchronize()
+        q.put((rank, f.cpu().numpy(), s.cpu().numpy(), Ds))
+        ctx.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_processes_allreduce_match_full_context():
+    """Transmitter sharding across two processes (world size 2, gloo all-reduce of g and D per step,
+    each rank with its own context on the same GPU, no kernel waiting on another rank): three
+    relaxed-FISTA steps leave both ranks in the state of cisor_step on the full context."""
+    import multiprocessing as mp
+    import socket
+
+    build.build()
+    cfg, f_true, angles, rx = synth.make_inputs("c1")
+    n, T, M = cfg["n"], cfg["T"], cfg["M"]
+    full = cisor.Cisor(n, cfg["delta"], angles, rx)
+    y = np.empty((T, M), np.complex64)
+    full.forward(c64(f_true), y_out=y, tol=1e-7, max_iter=3000)
+    s0 = c64(0.8 * f_true)
+    dev = torch.device("cuda")
+    g_full = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    full.grad(torch.from_numpy(s0).to(dev), torch.from_numpy(y).to(dev), g_full, tol=1e-6, max_iter=3000)
+    gamma = 0.05 / float(np.abs(g_full.cpu().numpy()).max())
+    ff, sf = torch.from_numpy(s0).to(dev), torch.from_numpy(s0).to(dev)
+    st_full = full.new_state(ff, sf, cfg["alpha"], gamma, cfg["tau"], cfg["tv_iters"], 0.0, 2.0)
+    D_full = []
+    for _ in range(3):
+        full.step(st_full, torch.from_numpy(y).to(dev), tol=1e-6, max_iter=3000, x0_mode=2)
+        D_full.append(st_full.D)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, y, s0, gamma, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, f, s, Ds in res:
+        assert rel(f, ff.cpu().numpy()) < 1e-5, rank
+        assert rel(s, sf.cpu().numpy()) < 1e-5, rank
+        assert rel(Ds, D_full) < 1e-5, rank
+    assert np.array_equal(res[0][1], res[1][1])
