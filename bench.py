@@ -236,20 +236,8 @@ def _oracle_rounds(cfg_name, T, tol, rounds, workers=None):
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(workers)
     queue = ctx.Queue()
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"  # one thread per process: the processes are the parallelism
-    try:
-        procs = [ctx.Process(target=_oracle_worker, args=(cfg_name, [w], tol, rounds, barrier, queue))
-                 for w in range(workers)]
-        for p in procs:
-            p.start()
-    finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+    procs = _spawn_single_threaded(ctx, _oracle_worker,
+                                   [(cfg_name, [w], tol, rounds, barrier, queue) for w in range(workers)])
     walls = []
     for _ in range(rounds):
         marks = [queue.get(timeout=3600) for _ in range(workers)]
@@ -367,9 +355,9 @@ def run_reference(args):
 
 
 def conv_sources_hash():
-    """Hash of the sources of the convolution kernels (conv.cu, regfft.cuh, fft.cuh)."""
+    """Hash of the sources of the convolution kernels (conv.cu, conv_cluster.cu, regfft.cuh, fft.cuh, dots.cuh)."""
     h = hashlib.sha256()
-    for name in ("conv.cu", "regfft.cuh", "fft.cuh"):
+    for name in ("conv.cu", "conv_cluster.cu", "regfft.cuh", "fft.cuh", "dots.cuh"):
         with open(os.path.join(ROOT, "paper_1708_01663_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -534,15 +522,31 @@ def _c4_worker(t, tol, rounds, barrier, queue):
         queue.put((t0, time.perf_counter()))
 
 
+def _spawn_single_threaded(ctx, target, argsets):
+    """Start one spawned process per argument tuple with one BLAS / OpenMP thread each."""
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"  # one thread per process: the processes are the parallelism
+    try:
+        procs = [ctx.Process(target=target, args=a) for a in argsets]
+        for p in procs:
+            p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return procs
+
+
 def _oracle_rounds_c4(tol, rounds=3):
     import multiprocessing as mp
     from paper_1708_01663_gb300 import train_fno
     workers = max(1, min(os.cpu_count() or 1, train_fno.T))
     ctx = mp.get_context("spawn")
     barrier, queue = ctx.Barrier(workers), ctx.Queue()
-    procs = [ctx.Process(target=_c4_worker, args=(w, tol, rounds, barrier, queue)) for w in range(workers)]
-    for p in procs:
-        p.start()
+    procs = _spawn_single_threaded(ctx, _c4_worker, [(w, tol, rounds, barrier, queue) for w in range(workers)])
     walls = []
     for _ in range(rounds):
         marks = [queue.get(timeout=3600) for _ in range(workers)]

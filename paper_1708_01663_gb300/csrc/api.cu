@@ -740,8 +740,12 @@ cisor_status cisor_set_rx_mask(cisor_ctx* c, const void* mask) {
 static bool two_stage_ok(const cisor_ctx* c) { return c->P == 128 || c->P == 256 || (c->dim == 2 && c->P == 512); }
 
 cisor_status cisor_set_cols_cta(cisor_ctx* c, int cols_nt) {
-  if (!c || (cols_nt != 512 && cols_nt != 256 && cols_nt != COLS_TWO_STAGE)) {
-    set_error("cisor_set_cols_cta: NULL context or cols_nt not 512 / 256 / %d", COLS_TWO_STAGE);
+  if (!c || (cols_nt != 512 && cols_nt != 256 && cols_nt != COLS_TWO_STAGE && cols_nt != COLS_CLUSTER)) {
+    set_error("cisor_set_cols_cta: NULL context or cols_nt not 512 / 256 / %d / %d", COLS_TWO_STAGE, COLS_CLUSTER);
+    return CISOR_ERR_INVALID_ARG;
+  }
+  if (cols_nt == COLS_CLUSTER && !conv_fused_ok(c)) {
+    set_error("cisor_set_cols_cta: the cluster pass (%d) needs a scalar 2D grid with P = 512", COLS_CLUSTER);
     return CISOR_ERR_INVALID_ARG;
   }
   if (cols_nt == COLS_TWO_STAGE && !two_stage_ok(c)) {
@@ -811,8 +815,10 @@ cisor_status cisor_autotune(cisor_ctx* c, int reps, int* cols_nt_out) {
   cudaEvent_t e0, e1;
   CISOR_CUDA(cudaEventCreate(&e0));
   CISOR_CUDA(cudaEventCreate(&e1));
-  const int variants[3] = {512, 256, COLS_TWO_STAGE};
-  const int nvar = two_stage_ok(c) ? 3 : 2;
+  int variants[4] = {512, 256, 0, 0};
+  int nvar = 2;
+  if (two_stage_ok(c)) variants[nvar++] = COLS_TWO_STAGE;
+  if (conv_fused_ok(c)) variants[nvar++] = COLS_CLUSTER;
   // transmitter chunks whose FFT intermediate takes about 16, 32 or 48 MB (L2 is 126 MB), and no chunking
   const int ntr = c->T * c->ncomp;
   const long long rbytes = (long long)c->rtstride * (long long)sizeof(float2);

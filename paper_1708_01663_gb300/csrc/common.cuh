@@ -241,6 +241,11 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
 
 // column shape code of the two-stage column kernels (P = 128, 256; P = 512 in 2D)
 constexpr int COLS_TWO_STAGE = 16;
+// shape code of the one-kernel pass by 8-CTA clusters (2D, P = 512, scalar fields; conv_cluster.cu)
+constexpr int COLS_CLUSTER = 8;
+cisor_status conv_fused_init();
+bool conv_fused_ok(const cisor_ctx* c);
+int conv_fused_pass(cisor_ctx* c, const ConvOp& op, int dk, cudaError_t* e);
 // EPI_MATVEC: out = src - m .* conv ; EPI_RESID: out = aux - (src - m .* conv);
 // EPI_CONV_ADD: out = conv + aux (aux may be null)
 enum { EPI_MATVEC = 0, EPI_RESID = 1, EPI_CONV_ADD = 2 };

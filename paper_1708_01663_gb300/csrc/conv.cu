@@ -373,28 +373,6 @@ __global__ void __launch_bounds__(256, TwoStage<P>::MINB)
   }
 }
 
-// Inner-product sets of the inverse-row epilogue.  The solver's three are
-// compiled with fixed operands; DOTS_ANY reads the operand codes of ConvOp.
-//   DOTS_RV : slot 0 <aux, y>               (<rhat, v>, v = A p)
-//   DOTS_TS : slot 1 <y, src>, slot 2 <y, y> (<t, s>, <t, t>, t = A s)
-//   DOTS_RES: slot 0 <aux, aux>, slot 2 <y, y> (<b, b>, <r, r>, r = b - A x)
-enum { DOTS_NONE = 0, DOTS_RV = 1, DOTS_TS = 2, DOTS_RES = 3, DOTS_ANY = 4 };
-
-static int dots_kind(const ConvOp& op) {
-  auto is = [&](int a0, int b0, int a1, int b1, int a2, int b2) {
-    return op.dot_a[0] == a0 && op.dot_b[0] == b0 && op.dot_a[1] == a1 && op.dot_b[1] == b1 &&
-           op.dot_a[2] == a2 && op.dot_b[2] == b2;
-  };
-  if (is(0, 0, 0, 0, 0, 0)) return DOTS_NONE;
-  if (is(OP_AUX, OP_Y, 0, 0, 0, 0)) return DOTS_RV;
-  if (is(0, 0, OP_Y, OP_SRC, OP_Y, OP_Y)) return DOTS_TS;
-  if (is(OP_AUX, OP_AUX, 0, 0, OP_Y, OP_Y)) return DOTS_RES;
-  return DOTS_ANY;
-}
-
-template <int DK> struct DotSlots {
-  static constexpr int MASK = DK == DOTS_NONE ? 0 : DK == DOTS_RV ? 1 : DK == DOTS_TS ? 6 : DK == DOTS_RES ? 5 : 7;
-};
 
 template <int P, int EPI, int DK>
 __global__ void __launch_bounds__(256) conv_rows_inv(const ConvOp op, const float2* __restrict__ tw_g,
@@ -572,7 +550,7 @@ static void launch_cols_2s(cisor_ctx* c, const ConvOp& op, int nslab, long long 
 
 template <int P, int MODE>
 static void cols_pass(cisor_ctx* c, const ConvOp& op, int nslab, long long es, long long slab) {
-  if (c->cols_nt == COLS_TWO_STAGE) {
+  if (c->cols_nt == COLS_TWO_STAGE || c->cols_nt == COLS_CLUSTER) {  // (combinations the cluster pass lacks)
     if (op.adjoint)
       launch_cols_2s<P, MODE, true>(c, op, nslab, es, slab);
     else
@@ -595,6 +573,16 @@ static void cols_pass(cisor_ctx* c, const ConvOp& op, int nslab, long long es, l
 template <int P>
 static cisor_status conv_chunk_t(cisor_ctx* c, const ConvOp& op) {
   typedef ConvCfg<P> C;
+  if constexpr (P == 512) {  // the one-kernel cluster pass where the shape asks for it and the combination exists
+    if (c->cols_nt == COLS_CLUSTER && conv_fused_ok(c)) {
+      cudaError_t e = cudaSuccess;
+      if (conv_fused_pass(c, op, dots_kind(op), &e)) {
+        CISOR_CUDA(e);
+        c->launches += 1;
+        return CISOR_OK;
+      }
+    }
+  }
   const int n = c->n;
   const RowGeo rg{n, c->nrows, c->rslab, c->rtstride};
   dim3 grow((c->nrows + C::RB - 1) / C::RB, op.ntx);
@@ -660,6 +648,7 @@ static cisor_status conv_pass_t(cisor_ctx* c, const ConvOp& op) {
 }
 
 cisor_status conv_init(int P) {
+  if (P == 512) CISOR_TRY(conv_fused_init());
   switch (P) {
     case 64: return conv_init_t<64>();
     case 128: return conv_init_t<128>();

@@ -4,6 +4,29 @@
 
 namespace cisor {
 
+// Inner-product sets of the inverse-row epilogue.  The solver's three are
+// compiled with fixed operands; DOTS_ANY reads the operand codes of ConvOp.
+//   DOTS_RV : slot 0 <aux, y>               (<rhat, v>, v = A p)
+//   DOTS_TS : slot 1 <y, src>, slot 2 <y, y> (<t, s>, <t, t>, t = A s)
+//   DOTS_RES: slot 0 <aux, aux>, slot 2 <y, y> (<b, b>, <r, r>, r = b - A x)
+enum { DOTS_NONE = 0, DOTS_RV = 1, DOTS_TS = 2, DOTS_RES = 3, DOTS_ANY = 4 };
+
+inline int dots_kind(const ConvOp& op) {
+  auto is = [&](int a0, int b0, int a1, int b1, int a2, int b2) {
+    return op.dot_a[0] == a0 && op.dot_b[0] == b0 && op.dot_a[1] == a1 && op.dot_b[1] == b1 &&
+           op.dot_a[2] == a2 && op.dot_b[2] == b2;
+  };
+  if (is(0, 0, 0, 0, 0, 0)) return DOTS_NONE;
+  if (is(OP_AUX, OP_Y, 0, 0, 0, 0)) return DOTS_RV;
+  if (is(0, 0, OP_Y, OP_SRC, OP_Y, OP_Y)) return DOTS_TS;
+  if (is(OP_AUX, OP_AUX, 0, 0, OP_Y, OP_Y)) return DOTS_RES;
+  return DOTS_ANY;
+}
+
+template <int DK> struct DotSlots {
+  static constexpr int MASK = DK == DOTS_NONE ? 0 : DK == DOTS_RV ? 1 : DK == DOTS_TS ? 6 : DK == DOTS_RES ? 5 : 7;
+};
+
 __device__ __forceinline__ float2 pick(int code, float2 y, float2 s, float2 a) {
   return code == OP_Y ? y : (code == OP_SRC ? s : a);
 }

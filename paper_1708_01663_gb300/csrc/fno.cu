@@ -98,10 +98,11 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 //   D (16 x 8):  d0 d1 (row g, col 2t, 2t+1), d2 d3 (row g + 8)
 __device__ __forceinline__ uint32_t bf_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
 __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-  hi = bf_bits(h0) | (bf_bits(h1) << 16);
-  lo = bf_bits(__float2bfloat16_rn(x0 - __bfloat162float(h0))) |
-       (bf_bits(__float2bfloat16_rn(x1 - __bfloat162float(h1))) << 16);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);  // one packed conversion, x0 in the low half
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 struct FragA {
   uint32_t h[4], l[4];
@@ -567,11 +568,13 @@ __global__ void __launch_bounds__(NTH, 2) fno_col(const float2* __restrict__ Tin
     auto Bt = [&](int k, int c) { return tf[2 * (c * TSP + (k & 127)) + (k >> 7)]; };
     const int mt = warp & 3, nt0 = (warp >> 2) * 2;
     float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    FragA a = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 0, g, t);
 #pragma unroll 2
-    for (int ks = 0; ks < 16; ++ks) {
-      const FragA a = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 16 * ks, g, t);
+    for (int ks = 0; ks < 16; ++ks) {  // the next k-step's table fragment is in flight during this one's MMAs
+      const FragA an = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 16 * ((ks + 1) & 15), g, t);
 #pragma unroll
       for (int j = 0; j < 2; ++j) mma3(d[j], a, load_b(Bt, 16 * ks, 8 * (nt0 + j), g, t));
+      a = an;
     }
     float* xf = reinterpret_cast<float*>(xs);
 #pragma unroll
@@ -612,17 +615,19 @@ __global__ void __launch_bounds__(NTH, 2) fno_col(const float2* __restrict__ Tin
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int j = 0; j < 4; ++j) d[h][j][0] = d[h][j][1] = d[h][j][2] = d[h][j][3] = 0.f;
+    FragA a0 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp), 0, g, t);
+    FragA a1 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + 1), 0, g, t);
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {
       FragB bq[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) bq[j] = load_b(By, 16 * ks, 8 * j, g, t);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const FragA a = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + h), 16 * ks, g, t);
+      for (int j = 0; j < 4; ++j) mma3(d[0][j], a0, bq[j]);
+      if (ks < 3) a0 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp), 16 * (ks + 1), g, t);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) mma3(d[h][j], a, bq[j]);
-      }
+      for (int j = 0; j < 4; ++j) mma3(d[1][j], a1, bq[j]);
+      if (ks < 3) a1 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + 1), 16 * (ks + 1), g, t);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h)

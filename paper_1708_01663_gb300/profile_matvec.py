@@ -6,8 +6,9 @@ Builds the tables of a named workload (seeded phantom, all transmitters, or
 the first ``--T``), autotunes the column-kernel shape (2 or 3 variants x
 (1 + 5) passes) and runs one untimed plus ``reps`` timed passes of
 y_t = A x_t over every transmitter through cisor_time_matvec.
-``--cols-cta 512|256|16`` sets the column-kernel shape instead of measuring
-it (16: the two-stage kernel), so that no convolution runs
+``--cols-cta 512|256|16|8`` sets the column-kernel shape instead of measuring
+it (16: the two-stage kernel, 8: the one-kernel cluster pass; ``--tx-chunk``
+the transmitter chunk), so that no convolution runs
 before the untimed pass and
 ``ncu --clock-control none --metrics gpu__time_duration.sum -k regex:conv_ -c k``
 (k = 3 kernels per pass in 2D, 5 in 3D) lists exactly that pass; a full-metric
@@ -27,7 +28,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--T", type=int, default=None)
-    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 16, 256, 512])
+    ap.add_argument("--cols-cta", type=int, default=0, choices=[0, 8, 16, 256, 512])
+    ap.add_argument("--tx-chunk", type=int, default=0)
     args = ap.parse_args()
     import torch
 
@@ -39,6 +41,7 @@ def main():
     fd = torch.from_numpy(np.ascontiguousarray(0.9 * f, dtype=np.complex64)).cuda()
     if args.cols_cta:
         ctx.set_cols_cta(args.cols_cta)
+        ctx.set_tx_chunk(args.tx_chunk)
         cols = args.cols_cta
     else:
         cols = ctx.autotune(reps=5)  # column-FFT CTA size chosen by measurement

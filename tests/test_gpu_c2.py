@@ -46,11 +46,11 @@ def c2():
     ctx.close()
 
 
-@pytest.mark.parametrize("shape", [512, 256, 16, "autotune"])
+@pytest.mark.parametrize("shape", [512, 256, 16, 8, "autotune"])
 def test_c2_full_size_sampled(c2, shape):
     cfg, f, ctx, ref, y_ref = c2
     if shape == "autotune":
-        assert ctx.autotune(reps=3) in (512, 256, 16)
+        assert ctx.autotune(reps=3) in (512, 256, 16, 8)
     else:
         ctx.set_cols_cta(shape)
     n, T, M = cfg["n"], cfg["T"], cfg["M"]

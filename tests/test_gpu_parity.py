@@ -154,12 +154,14 @@ def test_forward_two_stage_2d(n, P):
     assert rel(u, ref) <= 1e-4
 
 
-@pytest.mark.parametrize("shape", [512, 16])
+@pytest.mark.parametrize("shape", [512, 16, 8])
 def test_gradient_p512_shapes(shape):
     """D and the gradient at P = 512 (n = 130: most of each padded row and column
-    empty) with the three-stage kernels and with the two-stage row and column
-    kernels; exercises every prologue, epilogue and dot set of the solves plus
-    the G^H v + z epilogue of the gradient."""
+    empty) with the three-stage kernels, the two-stage column kernel and the
+    one-kernel cluster pass (shape 8: an 8-CTA cluster per transmitter, the
+    padded field in distributed shared memory); exercises every prologue,
+    epilogue and dot set of the solves plus the G^H v + z epilogue of the
+    gradient."""
     n, T, M = 130, 2, 24
     ctx, prob = make(n, T, M, 0.75 * n / 8 + 1.5, complex_f=True)
     assert ctx.P == 512
@@ -268,7 +270,8 @@ def test_solve_iterations_and_cols_cta():
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_column_shapes(n, pad, P, adjoint):
     """Every column-kernel shape (the three-stage kernel at 512 and 256 threads,
-    the two-stage kernel: 32 x 16 at P = 512, 16 x 16 at 256, 16 x 8 at 128)
+    the two-stage kernel: 32 x 16 at P = 512, 16 x 16 at 256, 16 x 8 at 128;
+    at P = 512 also the one-kernel cluster pass)
     against the oracle's A / A^H; a padded n leaves most of each column empty
     (ragged rows and columns)."""
     ctx, prob = make(n, 3, 8, 0.75 * n / 8 + 1.0, pad=pad)
@@ -277,7 +280,7 @@ def test_column_shapes(n, pad, P, adjoint):
     x = synth.random_field(8, (3, n, n))
     op = prob.AH if adjoint else prob.A
     ys = {}
-    for shape in (512, 256, 16):
+    for shape in ((512, 256, 16, 8) if P == 512 else (512, 256, 16)):
         ctx.set_cols_cta(shape)
         y = np.empty((3, n, n), np.complex64)
         ctx.apply_A(c64(f), c64(x), y, adjoint=adjoint)
@@ -299,7 +302,7 @@ def test_two_stage_shape_solves_and_autotunes():
     assert info.resid_max <= 1e-6
     ref, its, res = solve.solve_fields(prob, f, prob.u_in, tol=1e-12)
     assert rel(u, ref) < 1e-4
-    assert ctx.autotune(reps=2) in (512, 256, 16)
+    assert ctx.autotune(reps=2) in (512, 256, 16, 8)
     with pytest.raises(Exception):
         make(64, 1, 8, 6.0, complex_f=False)[0].set_cols_cta(8)
 
