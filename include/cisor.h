@@ -268,14 +268,16 @@ cisor_status cisor_autotune(cisor_ctx* ctx, int reps, int* cols_nt_out);
  * shape).  Results are identical whatever the chunk. */
 cisor_status cisor_set_tx_chunk(cisor_ctx* ctx, int tx_chunk);
 
-/* How a solve's BiCGSTAB iterations are driven.  device_loop = 1 (the
- * default): the whole solve is ONE CUDA-graph launch whose WHILE node repeats
- * a captured chunk of iterations until no transmitter is active (a device-side
- * condition kernel decides; the loop count is capped at max_iter / chunk + 2),
- * so the host waits once per solve.  device_loop = 0: the host replays a
- * chunk graph and reads the active flags after every chunk.  Results are
- * identical; where conditional graph nodes are unavailable the library falls
- * back to 0 by itself. */
+/* How a solve's BiCGSTAB iterations are driven.  device_loop = 1: the whole
+ * solve is ONE CUDA-graph launch whose WHILE node repeats a captured chunk of
+ * iterations until no transmitter is active (a device-side condition kernel
+ * decides; the loop count is capped at max_iter / chunk + 2), so the host
+ * waits once per solve.  device_loop = 0 (the default for a context): the host
+ * replays a chunk graph and reads the active flags after every chunk; kernel
+ * profilers list the kernels of such graphs, while they cannot look inside a
+ * graph with conditional nodes (only the whole graph).  Results are identical
+ * and so, measured, is the time at the benchmark sizes; where conditional
+ * graph nodes are unavailable the library falls back to 0 by itself. */
 cisor_status cisor_set_solve_loop(cisor_ctx* ctx, int device_loop);
 
 /* The context's current column shape (512, 256 or 16) and transmitter chunk
@@ -314,7 +316,7 @@ typedef struct cisor_batch cisor_batch;
  * cisor_autotune on each. */
 cisor_status cisor_batch_create(cisor_batch** out, const cisor_geometry* geoms, int nprob, void* stream,
                                 int autotune);
-/* As cisor_set_solve_loop for a batch: device_loop = 1 (default) runs each
+/* As cisor_set_solve_loop for a batch: device_loop = 1 (the batch default) runs each
  * solve of all problems as one graph launch with a device-side loop over
  * chunks of iterations of every problem; 0 replays a chunk graph per host
  * iteration. */

@@ -294,7 +294,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   c->rx_pos.assign(g->rx_pos, g->rx_pos + (size_t)d * g->M);
   c->user_stream = (cudaStream_t)stream;
   c->graph_chunk = 4;
-  c->use_while = 1;
+  c->use_while = 0;  // host-driven chunks by default: profilers list the kernels of these graphs
   c->cols_nt = 512;
   conv_geometry(c);
   {

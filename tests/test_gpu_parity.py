@@ -336,3 +336,23 @@ def test_tx_chunks_keep_results(n, T):
             ref["u"] = u
         else:
             assert rel(u, ref["u"]) < 1e-5
+
+
+def test_device_side_solve_loop_matches_host_loop():
+    """The whole solve as one graph launch (a WHILE node over chunks of BiCGSTAB iterations, ended by
+    a device-side condition kernel) gives the fields, iteration counts and residuals of the
+    host-driven chunk loop, and the oracle's fields (Eq. 13)."""
+    n, T = 64, 5
+    ctx, prob = make(n, T, 8, 6.0, complex_f=True)
+    f = c64(synth.ellipse_phantom(n, 4, (0.0, 0.8), 41, 0.05))
+    res = {}
+    for mode in (False, True):
+        ctx.set_solve_loop(mode)
+        u = np.empty((T, n, n), np.complex64)
+        st, info = ctx.forward(f, u_out=u, tol=1e-6, max_iter=3000)
+        assert info.resid_max <= 1e-6
+        res[mode] = (u, ctx.solve_iterations().tolist())
+    assert res[True][1] == res[False][1]
+    assert rel(res[True][0], res[False][0]) < 1e-6
+    ref, _, _ = solve.solve_fields(prob, f.astype(np.complex128), prob.u_in, tol=1e-12)
+    assert rel(res[True][0], ref) < 1e-4
