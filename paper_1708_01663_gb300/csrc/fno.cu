@@ -47,6 +47,8 @@
 #include <new>
 
 #include "common.cuh"
+#include "gelu.cuh"
+#include "tc5.cuh"
 
 namespace cisor {
 
@@ -82,14 +84,15 @@ constexpr int PART_MAX = PART_P;
 constexpr int RFP = FN + 8, RIP = 2 * FM + 8, CFP = 2 * FN + 8, CIP = 2 * FKX + 8;
 constexpr int T_RF = 2 * FM * RFP, T_RI = FN * RIP, T_CF = 2 * FKX * CFP, T_CI = 2 * FN * CIP;
 constexpr int T_ROW = 2 * (T_RF + T_RI);        // bf16 of the row tables (hi and lo), copied to shared memory
-constexpr int T_ALL = T_ROW + 2 * (T_CF + T_CI);  // + the column tables (read through L1)
+constexpr int T_COLS = T_ROW + 2 * (T_CF + T_CI);  // + the column tables (read through L1)
+// Row-DFT tables of the tcgen05 row kernel, in the tensor cores' core-matrix layout (tc5.cuh), hi and lo
+// planes of 128 x 32 BF16 each: RowI A operand E^T [128 ix][32 kyc] (LBO 128, SBO 512) and RowF B operand
+// E [32 kyc][128 ix] (LBO 128, SBO 2048).
+constexpr int T_TCP = FN * 2 * FM;                 // BF16 per plane
+constexpr int T_ALL = T_COLS + 4 * T_TCP;
 constexpr int WP = FC + 8;                        // pitch (bf16) of a 32-wide weight row in shared memory
 constexpr int P1TP = FH + 8;                      // pitch (bf16) of P1^T rows
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
 
 // ------------------------------------------------------------------ tensor-core tiles
 // m16n8k16 fragments (PTX ISA, mma.sync .bf16): lane = 4 g + t;
@@ -400,138 +403,268 @@ __global__ void __launch_bounds__(NTH, 2) fno_lift_fwd(const float2* __restrict_
 // v_{l+1} = GELU(pre) (or pre), then either the row DFT of v_{l+1} for the
 // next layer (PROJ = 0) or the projection out = P2 GELU(P1 v + c1) + c2 and,
 // when x0 is given, the warm start x0 = u_in (1 + out_0 + j out_1) (PROJ = 1).
-// Persistent over (sample, row block) items: the tables and weights are
-// staged once per CTA, and the next item's v_l and Z blocks are copied in
-// (cp.async) while the current item's activation, row DFT or projection runs.
-constexpr int SM_ROW = (2 * FC * NPP + FC) * 4 + BLK * 8 + T_ROW * 2 + FC * WP * 2;
+// Persistent over (sample, row block) items, on the fifth-generation tensor
+// cores (tcgen05): one thread issues each GEMM as whole tiles, the operands
+// staged once per item in BF16 hi / lo core-matrix layout (tc5.cuh), the
+// accumulators in tensor memory:
+//   D[ix][32 r + c] = sum_kyc E(ix, kyc) Z(32 r + c, kyc)   M 128, N 64, K 32  (inverse row DFT, transposed)
+//   D[ix][32 r + o] += sum_i v(r, ix, i) W[o][i]             M 128, N 32, K 32  (W v, one tile per row r)
+//   D3[32 r + c][kyc] = sum_ix v'(r, ix, c) E(ix, kyc)        M 64,  N 32, K 128 (row DFT of v_{l+1})
+//   D4_r[ix][hid] = sum_c v'(r, ix, c) P1[hid][c]            M 128, N 128, K 32 (projection, PROJ)
+// The first two accumulate into the same columns, so TMEM holds pre - b.
+// Thread (warp w, lane l) owns pixel ix = 32 (w % 4) + l of image row r = w / 4:
+// TMEM lane ix holds its row of D and D4_r, so pre = D + b, the GELU, the
+// global stores of pre and v_{l+1} (consecutive lanes, consecutive addresses)
+// and, for the projection, the 128 hidden units and P2 of its pixel stay in
+// that thread.  D3 (M = 64) sits in lanes 16 q + m of warp quarter q.  The
+// next item's v_l and Z values are loaded into registers while the current
+// item's GEMMs and epilogues run.  Every wait on the MMAs is bounded; on a
+// timeout the kernel records it in *err, frees its tensor memory and returns.
+constexpr int TC_LBO = 128, TC_SBO = 512;             // K = 32 operands: 4 K groups of 128 bytes per 8 rows
+constexpr int TC_RF_LBO = 160, TC_RF_SBO = 16 * 160;  // row-DFT A operand (K = 128), padded: conflict-free staging
+constexpr int TC_TAB = T_TCP * 2;                     // bytes of one table plane
+constexpr int TC_PL_MIX = NP * FC * 2;                // bytes of one plane of a [256 p][32 c] operand
+constexpr int TC_PL_RF = 8 * TC_RF_SBO;               // bytes of one plane of the [64 rr][128 ix] operand
+constexpr int TC_PL_Z = 2 * FC * 2 * FM * 2;          // bytes of one plane of Z [64 rr][32 kyc]
+constexpr int TC_AREG = 2 * (TC_PL_RF > TC_PL_MIX ? TC_PL_RF : TC_PL_MIX);
+constexpr int TSM_A = 4 * TC_TAB, TSM_Z = TSM_A + TC_AREG, TSM_W = TSM_Z + 2 * TC_PL_Z, TSM_BIAS = TSM_W + FC * FC * 2,
+              TSM_C1 = TSM_BIAS + FC * 4, TSM_P2 = TSM_C1 + FH * 4, SM_ROW_TC = TSM_P2 + 2 * FH * 4;
+constexpr int TC_WAIT = 1 << 20;  // polls of an MMA completion barrier before giving up
 template <int PROJ>
-__global__ void __launch_bounds__(NTH, 2) fno_row_fwd(const float* __restrict__ vin, const float2* __restrict__ Z,
-                                                      const __nv_bfloat16* __restrict__ wbf,
-                                                      const float* __restrict__ pm, long long woff, long long boff,
-                                                      const __nv_bfloat16* __restrict__ tabs, int act, int B,
-                                                      float* __restrict__ pre_out, float* __restrict__ vout,
-                                                      float2* __restrict__ T1, float2* __restrict__ out,
-                                                      const float2* __restrict__ u_in, float2* __restrict__ x0) {
-  extern __shared__ __align__(16) float smem[];
-  float* vs = smem;                                        // [FC][NPP] v_l
-  float* ps = vs + FC * NPP;                               // [FC][NPP] pre, then v_{l+1}
-  float* bias = ps + FC * NPP;                             // [FC]
-  float2* zs = reinterpret_cast<float2*>(bias + FC);       // [BLK] Z block
-  __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(zs + BLK);  // [T_ROW]; P1, c1, P2 in the RowF part (PROJ)
-  __nv_bfloat16* ws = tb + T_ROW;                          // [FC][WP] W_l
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+__global__ void __launch_bounds__(NTH, 2) fno_row_tc(const float* __restrict__ vin, const float2* __restrict__ Z,
+                                                     const __nv_bfloat16* __restrict__ wbf,
+                                                     const float* __restrict__ pm, long long woff, long long boff,
+                                                     const __nv_bfloat16* __restrict__ tabs, int act, int B,
+                                                     float* __restrict__ pre_out, float* __restrict__ vout,
+                                                     float2* __restrict__ T1, float2* __restrict__ out,
+                                                     const float2* __restrict__ u_in, float2* __restrict__ x0,
+                                                     int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  constexpr uint32_t NCOL = PROJ ? 256 : 128;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q4 = warp & 3, r = warp >> 2, ix = 32 * q4 + lane;  // this thread's pixel (r, ix) and TMEM lane
+  const int zr = tid & 63, zq = tid >> 6;                         // this thread's Z row and K group
   const int items = B * NIB;
+  if (blockIdx.x >= items) return;
+  float* bias = reinterpret_cast<float*>(sm + TSM_BIAS);
+  float* c1 = reinterpret_cast<float*>(sm + TSM_C1);
+  float* p2 = reinterpret_cast<float*>(sm + TSM_P2);
+  // tables (RowI A; RowF B, or P1 for the projection), W, bias
+  cta_copy(sm, tabs + T_COLS, (PROJ ? 2 : 4) * TC_TAB);
+  for (int e = tid; e < FC * FC; e += NTH)
+    *reinterpret_cast<__nv_bfloat16*>(sm + TSM_W + core_off(e / FC, e % FC, TC_LBO, TC_SBO)) = wbf[woff + e];
+  if (tid < FC) bias[tid] = pm[boff + tid];
+  if (PROJ) {
+    for (int e = tid; e < FH * FC; e += NTH)
+      *reinterpret_cast<__nv_bfloat16*>(sm + 2 * TC_TAB + core_off(e / FC, e % FC, TC_LBO, TC_SBO)) = wbf[F_P1 + e];
+    for (int i = tid; i < FH; i += NTH) c1[i] = pm[F_C1 + i];
+    for (int i = tid; i < 2 * FH; i += NTH) p2[i] = __bfloat162float(wbf[F_P2 + i]);
+  }
+  if (tid == 0) mbar_init(&mbar);
+  if (warp == 0) tmem_alloc(&tslot, NCOL);
+  cp_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t s0 = smem_addr(sm);
+  const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);  // this warp's TMEM lane quarter
+  const float c20 = PROJ ? pm[F_C2] : 0.f, c21 = PROJ ? pm[F_C2 + 1] : 0.f;
+  float nv[FC];
+  float2 nz[4];
   auto fetch = [&](int it) {
     const int b = it / NIB, iyb = it % NIB;
-    load_planar(vs, vin, b, (long long)iyb * RB * FN);
-    cta_copy(zs, Z + ((long long)b * NIB + iyb) * BLK, BLK * 8);
+    const float* src = vin + (long long)b * FC * FNN + (long long)(iyb * RB + r) * FN + ix;
+#pragma unroll
+    for (int c = 0; c < FC; ++c) nv[c] = __ldg(src + (long long)c * FNN);
+    const float2* zb = Z + ((long long)b * NIB + iyb) * BLK;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) nz[m] = __ldg(zb + ((4 * zq + m) * FC + (zr & 31)) * RB + (zr >> 5));
   };
-  if (blockIdx.x >= items) return;
-  cta_copy(tb + (PROJ ? 2 * T_RF : 0), tabs + (PROJ ? 2 * T_RF : 0), (PROJ ? 2 * T_RI : T_ROW) * 2);
+  // 32 values of one [256 p][32 c] row p into the hi / lo planes at byte offset a (uint4 stores)
+  auto stage_row32 = [&](int a, int p, const float (&x)[FC]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint4 h, l;
+      split_pair(x[8 * j + 0], x[8 * j + 1], h.x, l.x);
+      split_pair(x[8 * j + 2], x[8 * j + 3], h.y, l.y);
+      split_pair(x[8 * j + 4], x[8 * j + 5], h.z, l.z);
+      split_pair(x[8 * j + 6], x[8 * j + 7], h.w, l.w);
+      const int o = core_off(p, 8 * j, TC_LBO, TC_SBO);
+      *reinterpret_cast<uint4*>(sm + a + o) = h;
+      *reinterpret_cast<uint4*>(sm + a + TC_PL_MIX + o) = l;
+    }
+  };
+  auto sync_mma = [&]() {  // thread-written operands visible to the tensor cores, TMEM reads ordered
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  };
+  uint32_t ph = 0;
+  bool failed = false;
+  auto wait_mma = [&]() {  // true if the committed MMAs completed in every thread's view
+    const bool ok = mbar_wait(&mbar, ph, TC_WAIT);
+    ph ^= 1u;
+    tc_fence_after();
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      failed = true;
+    }
+    return !failed;
+  };
+  const uint32_t id_i = tc_idesc_bf16(128, 64), id_w = tc_idesc_bf16(128, 32), id_f = tc_idesc_bf16(64, 32),
+                 id_p = tc_idesc_bf16(128, 128);
   fetch(blockIdx.x);
-  load_w(wbf + woff, ws, nullptr);
-  if (threadIdx.x < FC) bias[threadIdx.x] = pm[boff + threadIdx.x];
-  // projection weights in the (unused) RowF part of the table area: P1 [FH][WP], c1 [FH], P2 [2][FH]
-  __nv_bfloat16* p1 = tb;
-  float* c1 = reinterpret_cast<float*>(p1 + FH * WP);
-  float* p2 = c1 + FH;
-  if (PROJ) {
-    for (int e = threadIdx.x; e < FH * FC; e += NTH) p1[(e / FC) * WP + e % FC] = wbf[F_P1 + e];
-    for (int i = threadIdx.x; i < FH; i += NTH) c1[i] = pm[F_C1 + i];
-    for (int i = threadIdx.x; i < 2 * FH; i += NTH) p2[i] = __bfloat162float(wbf[F_P2 + i]);
-  }
-  cp_wait_all();
-  __syncthreads();
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int b = it / NIB, iyb = it % NIB, iy0 = iyb * RB;
     const long long pix0 = (long long)iy0 * FN;
     const long long gbase = (long long)b * FC * FNN + pix0;
-    row_inverse(zs, tb, ps, false);
-    __syncthreads();
-    pixel_mix([&](int p, int i) { return vs[i * NPP + p]; }, ws,
-              [&](int p, int o, float v) { ps[o * NPP + p] += v + bias[o]; });
-    __syncthreads();
+    // stage v_l (A of W v) and Z (B of the inverse row DFT), then fetch the next item
+    stage_row32(TSM_A, FN * r + ix, nv);
+    {
+      uint4 h, l;
+      split_pair(nz[0].x, nz[0].y, h.x, l.x);
+      split_pair(nz[1].x, nz[1].y, h.y, l.y);
+      split_pair(nz[2].x, nz[2].y, h.z, l.z);
+      split_pair(nz[3].x, nz[3].y, h.w, l.w);
+      const int o = core_off(zr, 8 * zq, TC_LBO, TC_SBO);
+      *reinterpret_cast<uint4*>(sm + TSM_Z + o) = h;
+      *reinterpret_cast<uint4*>(sm + TSM_Z + TC_PL_Z + o) = l;
+    }
     const int nxt = it + gridDim.x;
-    if (nxt < items) fetch(nxt);  // vs and zs are free until the end of this item
-    // pre to global (training), activation in place, v_{l+1} to global
-    planar_pass(ps, gbase, [&](float4& x, long long gi) {
-      if (pre_out) *reinterpret_cast<float4*>(pre_out + gi) = x;
-      if (act) x = make_float4(gelu_f(x.x), gelu_f(x.y), gelu_f(x.z), gelu_f(x.w));
-      if (vout) *reinterpret_cast<float4*>(vout + gi) = x;
-    });
-    __syncthreads();
-    if (!PROJ) {  // the row DFT of v_{l+1}, written to the block's T1 slot from the fragments
-      float2* dst = T1 + ((long long)b * NIB + iyb) * BLK;
-      auto A = [&](int rr, int ix) { return ps[(rr & 31) * NPP + (rr >> 5) * FN + ix]; };
-      const uint32_t *th = tab_rf(tb, 0), *tl = tab_rf(tb, 1);
-      const int mt = warp & 3, nt0 = (warp >> 2) * 2;
-      float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll 2
-      for (int ks = 0; ks < FN / 16; ++ks) {
-        const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
+    if (nxt < items) fetch(nxt);
+    sync_mma();
+    if (tid == 0) {
+      // inverse row DFT: E (hi, lo) x Z (hi, lo), three products per K step
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          uint32_t bh[2], bl[2];
-          load_b_tab(th, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bh);
-          load_b_tab(tl, RFP / 2, 16 * ks, 8 * (nt0 + j), g, t, bl);
-          mma3t(d[j], a, bh, bl);
-        }
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint32_t ah = s0 + ks * 2 * TC_LBO, al = ah + TC_TAB;
+        const uint32_t bh = s0 + TSM_Z + ks * 2 * TC_LBO, bl = bh + TC_PL_Z;
+        tc_mma(tmem, tc_desc(ah, TC_LBO, TC_SBO), tc_desc(bh, TC_LBO, TC_SBO), id_i, ks > 0);
+        tc_mma(tmem, tc_desc(al, TC_LBO, TC_SBO), tc_desc(bh, TC_LBO, TC_SBO), id_i, 1);
+        tc_mma(tmem, tc_desc(ah, TC_LBO, TC_SBO), tc_desc(bl, TC_LBO, TC_SBO), id_i, 1);
       }
+      // + W v, row by row into the same columns (W exact in BF16, v as hi + lo)
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int rr = 16 * mt + g + 8 * h, ky = 4 * (nt0 + j) + t;
-          dst[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[j][2 * h], d[j][2 * h + 1]);
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t ah = s0 + TSM_A + rr * (TC_PL_MIX / 2) + ks * 2 * TC_LBO, al = ah + TC_PL_MIX;
+          const uint64_t bw = tc_desc(s0 + TSM_W + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+          tc_mma(tmem + 32 * rr, tc_desc(ah, TC_LBO, TC_SBO), bw, id_w, 1);
+          tc_mma(tmem + 32 * rr, tc_desc(al, TC_LBO, TC_SBO), bw, id_w, 1);
         }
-    } else {  // projection: z = P1 v + c1 (GEMM M = NP, N = FH, K = FC), h = GELU(z), out = P2 h + c2
-      auto A = [&](int p, int c) { return ps[c * NPP + p]; };
-      const uint32_t* p132 = reinterpret_cast<const uint32_t*>(p1);
-      const float c20 = pm[F_C2], c21 = pm[F_C2 + 1];
+      tc_commit(&mbar);
+    }
+    if (!wait_mma()) break;
+    // epilogue: pre = D + b (to global when training), v_{l+1} = act(pre) to global, staged as the next A
+    float v[FC];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int mt = 2 * warp + h;
-        const FragA a0 = load_a(A, 16 * mt, 0, g, t), a1 = load_a(A, 16 * mt, 16, g, t);
-        float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [row g / g + 8][out 0 / 1]
-#pragma unroll 4
-        for (int nt = 0; nt < FH / 8; ++nt) {
-          uint32_t b0[2], b1[2];
-          load_b_tab(p132, WP / 2, 0, 8 * nt, g, t, b0);
-          load_b_tab(p132, WP / 2, 16, 8 * nt, g, t, b1);
-          float d[4] = {0.f, 0.f, 0.f, 0.f};
-          mma2(d, a0, b0);
-          mma2(d, a1, b1);
+    for (int j = 0; j < 4; ++j) {
+      float d[8];
+      tmem_ld8(tl + 32 * r + 8 * j, d);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int hid = 8 * nt + 2 * t + (e & 1);
-            const float hv = gelu_f(d[e] + c1[hid]);
-            o[e >> 1][0] += p2[hid] * hv;
-            o[e >> 1][1] += p2[FH + hid] * hv;
-          }
-        }
+      for (int k = 0; k < 8; ++k) v[8 * j + k] = d[k] + bias[8 * j + k];
+    }
+    {
+      const long long g0 = gbase + (long long)r * FN + ix;
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            o[r][k] += __shfl_xor_sync(0xffffffffu, o[r][k], 1);
-            o[r][k] += __shfl_xor_sync(0xffffffffu, o[r][k], 2);
-          }
-        if (t == 0)
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const long long pix = (long long)b * FNN + pix0 + 16 * mt + g + 8 * r;
-            const float2 e = make_float2(o[r][0] + c20, o[r][1] + c21);
-            if (out) out[pix] = e;
-            if (x0) {
-              const float2 u = u_in[pix];
-              x0[pix] = c_add(u, c_mul(u, e));
-            }
-          }
+      for (int c = 0; c < FC; ++c) {
+        if (pre_out) pre_out[g0 + (long long)c * FNN] = v[c];
+        if (act) v[c] = gelu_f(v[c]);
+        if (vout) vout[g0 + (long long)c * FNN] = v[c];
       }
     }
-    cp_wait_all();
+    if (!PROJ) {
+      // A of the row DFT, [32 r + c][ix]: lanes ix, ix + 1 exchange so that each stores a 32-bit pair
+      const bool odd = lane & 1;
+#pragma unroll
+      for (int m = 0; m < FC / 2; ++m) {
+        const float y = __shfl_xor_sync(0xffffffffu, odd ? v[2 * m] : v[2 * m + 1], 1);
+        const int row = 32 * r + 2 * m + (odd ? 1 : 0), k = ix & ~1;
+        uint32_t h, l;
+        if (odd)
+          split_pair(y, v[2 * m + 1], h, l);
+        else
+          split_pair(v[2 * m], y, h, l);
+        const int o = core_off(row, k, TC_RF_LBO, TC_RF_SBO);
+        *reinterpret_cast<uint32_t*>(sm + TSM_A + o) = h;
+        *reinterpret_cast<uint32_t*>(sm + TSM_A + TC_PL_RF + o) = l;
+      }
+    } else {
+      stage_row32(TSM_A, FN * r + ix, v);
+    }
+    sync_mma();
+    if (tid == 0) {
+      if (!PROJ) {  // row DFT: v' (hi, lo) x E (hi, lo) into columns 64 ..
+#pragma unroll
+        for (int ks = 0; ks < FN / 16; ++ks) {
+          const uint32_t ah = s0 + TSM_A + ks * 2 * TC_RF_LBO, al = ah + TC_PL_RF;
+          const uint32_t bh = s0 + 2 * TC_TAB + ks * 2 * TC_LBO, bl = bh + TC_TAB;
+          tc_mma(tmem + 64, tc_desc(ah, TC_RF_LBO, TC_RF_SBO), tc_desc(bh, TC_LBO, 2048), id_f, ks > 0);
+          tc_mma(tmem + 64, tc_desc(al, TC_RF_LBO, TC_RF_SBO), tc_desc(bh, TC_LBO, 2048), id_f, 1);
+          tc_mma(tmem + 64, tc_desc(ah, TC_RF_LBO, TC_RF_SBO), tc_desc(bl, TC_LBO, 2048), id_f, 1);
+        }
+      } else {  // z = P1 v' per row r into columns 128 r ..
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t ah = s0 + TSM_A + rr * (TC_PL_MIX / 2) + ks * 2 * TC_LBO, al = ah + TC_PL_MIX;
+            const uint64_t bp = tc_desc(s0 + 2 * TC_TAB + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+            tc_mma(tmem + 128 * rr, tc_desc(ah, TC_LBO, TC_SBO), bp, id_p, ks > 0);
+            tc_mma(tmem + 128 * rr, tc_desc(al, TC_LBO, TC_SBO), bp, id_p, 1);
+          }
+      }
+      tc_commit(&mbar);
+    }
+    if (!wait_mma()) break;
+    if (!PROJ) {  // T1 block [ky][c][r] from rows 32 r + c (lanes 16 q + m), columns split by warp half
+      float2* dst = T1 + ((long long)b * NIB + iyb) * BLK;
+      const int rr = 16 * q4 + lane;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float d[8];
+        tmem_ld8(tl + 64 + 16 * r + 8 * j, d);
+        if (lane < 16)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int ky = 8 * r + 4 * j + k;
+            dst[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[2 * k], d[2 * k + 1]);
+          }
+      }
+    } else {  // out = P2 GELU(z + c1) + c2 for this thread's pixel; warm start x0 = u_in (1 + out)
+      float o0 = c20, o1 = c21;
+#pragma unroll 2
+      for (int j = 0; j < FH / 8; ++j) {
+        float d[8];
+        tmem_ld8(tl + 128 * r + 8 * j, d);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int hid = 8 * j + k;
+          const float hv = gelu_f(d[k] + c1[hid]);
+          o0 += p2[hid] * hv;
+          o1 += p2[FH + hid] * hv;
+        }
+      }
+      const long long pix = (long long)b * FNN + pix0 + (long long)r * FN + ix;
+      const float2 e = make_float2(o0, o1);
+      if (out) out[pix] = e;
+      if (x0) {
+        const float2 u = u_in[pix];
+        x0[pix] = c_add(u, c_mul(u, e));
+      }
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOL);
 }
 
 // Column kernel, one (ky, sample): X = ColF(T1) over iy to the 32 kept kx; forward: Y = mix_R(X) x w_ky / 128^2,
@@ -1068,6 +1201,16 @@ __global__ void fno_tables(__nv_bfloat16* __restrict__ tabs) {
     }
     hi = tabs + T_ROW + 2 * T_CF + j;
     lo = hi + T_CI;
+  } else if (i < T_RF + T_RI + T_CF + T_CI + T_TCP) {  // tcgen05 RowI A: row ix, K = kyc
+    const int j = i - (T_RF + T_RI + T_CF + T_CI), ix = j / (2 * FM), kyc = j % (2 * FM);
+    v = row_entry(ix, kyc);
+    hi = tabs + T_COLS + core_off(ix, kyc, 128, 512) / 2;
+    lo = hi + T_TCP;
+  } else if (i < T_RF + T_RI + T_CF + T_CI + 2 * T_TCP) {  // tcgen05 RowF B: row kyc, K = ix
+    const int j = i - (T_RF + T_RI + T_CF + T_CI + T_TCP), kyc = j / FN, ix = j % FN;
+    v = row_entry(ix, kyc);
+    hi = tabs + T_COLS + 2 * T_TCP + core_off(kyc, ix, 128, 2048) / 2;
+    lo = hi + T_TCP;
   } else {
     return;
   }
@@ -1149,6 +1292,8 @@ struct cisor_fno {
   float *v[FL + 1], *pre[FL], *dout, *dvA, *dvB, *loss;
   float2 *Xst[FL], *dYst, *T1, *Zb, *out, *fbuf, *ubuf, *tbuf, *usc;
   float* h_loss;
+  int* dflag;   // set by a kernel whose bounded wait on the tensor cores gave up
+  int* h_flag;  // pinned copy of dflag
 };
 
 namespace {
@@ -1168,8 +1313,8 @@ unsigned grid_of(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cisor_status fno_kernel_attrs() {
   CISOR_CUDA(cudaFuncSetAttribute(fno_lift_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_LIFT));
-  CISOR_CUDA(cudaFuncSetAttribute(fno_row_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW));
-  CISOR_CUDA(cudaFuncSetAttribute(fno_row_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_row_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW_TC));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_row_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW_TC));
   CISOR_CUDA(cudaFuncSetAttribute(fno_col<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
   CISOR_CUDA(cudaFuncSetAttribute(fno_col<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
   CISOR_CUDA(cudaFuncSetAttribute(fno_row_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_RBWD));
@@ -1193,11 +1338,11 @@ cisor_status fno_forward_core(cisor_fno* F, int fps, int B, int train, const flo
     const int last = l == FL - 1;
     float* pre = train ? F->pre[l] : nullptr;
     if (!last) {
-      fno_row_fwd<0><<<gper, NTH, SM_ROW, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 1, B, pre,
-                                              F->v[l + 1], F->T1, nullptr, nullptr, nullptr);
+      fno_row_tc<0><<<gper, NTH, SM_ROW_TC, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 1, B, pre,
+                                                 F->v[l + 1], F->T1, nullptr, nullptr, nullptr, F->dflag);
     } else {
-      fno_row_fwd<1><<<gper, NTH, SM_ROW, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 0, B, pre,
-                                              train ? F->v[FL] : nullptr, nullptr, F->out, xin, x0);
+      fno_row_tc<1><<<gper, NTH, SM_ROW_TC, s>>>(F->v[l], F->Zb, F->wbf, F->pm, f_W(l), f_B(l), F->tabs, 0, B, pre,
+                                                 train ? F->v[FL] : nullptr, nullptr, F->out, xin, x0, F->dflag);
     }
     CISOR_CUDA(cudaGetLastError());
   }
@@ -1255,9 +1400,22 @@ bool bad_batch(cisor_fno* F, int B) {
   return false;
 }
 
+// waits for the FNO stream; an error if a tensor-core wait timed out in the work it ran (the flag is reset)
+cisor_status fno_sync(cisor_fno* F) {
+  CISOR_CUDA(cudaMemcpyAsync(F->h_flag, F->dflag, sizeof(int), cudaMemcpyDeviceToHost, F->stream));
+  CISOR_CUDA(cudaStreamSynchronize(F->stream));
+  if (*F->h_flag) {
+    CISOR_CUDA(cudaMemsetAsync(F->dflag, 0, sizeof(int), F->stream));
+    CISOR_CUDA(cudaStreamSynchronize(F->stream));
+    set_error("FNO: a wait on the tensor cores timed out; the outputs of this call are invalid");
+    return CISOR_ERR_CUDA;
+  }
+  return CISOR_OK;
+}
+
 cisor_status mean_loss(cisor_fno* F, int B, double* loss) {
   CISOR_CUDA(cudaMemcpyAsync(F->h_loss, F->loss, sizeof(float) * B, cudaMemcpyDeviceToHost, F->stream));
-  CISOR_CUDA(cudaStreamSynchronize(F->stream));
+  CISOR_TRY(fno_sync(F));
   double s = 0.0;
   for (int b = 0; b < B; ++b) s += F->h_loss[b];
   if (loss) *loss = s / B;
@@ -1278,6 +1436,8 @@ void fno_free(cisor_fno* F) {
     if (F->Xst[l]) cudaFree(F->Xst[l]);
   }
   if (F->h_loss) cudaFreeHost(F->h_loss);
+  if (F->h_flag) cudaFreeHost(F->h_flag);
+  if (F->dflag) cudaFree(F->dflag);
   if (F->ev_a) cudaEventDestroy(F->ev_a);
   if (F->ev_b) cudaEventDestroy(F->ev_b);
   if (F->stream) cudaStreamDestroy(F->stream);
@@ -1340,7 +1500,8 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
                 {(void**)&F->fbuf, fld},
                 {(void**)&F->ubuf, fld},
                 {(void**)&F->tbuf, fld},
-                {(void**)&F->usc, fld}};
+                {(void**)&F->usc, fld},
+                {(void**)&F->dflag, sizeof(int)}};
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return fail(e, "FNO cudaMalloc");
@@ -1351,6 +1512,7 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
     if (e == cudaSuccess) e = cudaMalloc((void**)&F->Xst[l], md);
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_loss, sizeof(float) * max_batch);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_flag, sizeof(int));
   if (e != cudaSuccess) return fail(e, "FNO cudaMalloc");
   cisor_status st = fno_kernel_attrs();
   if (st != CISOR_OK) {
@@ -1359,10 +1521,11 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
   }
   fno_init<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F_TOTAL, seed);
   fno_to_bf16<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F->wbf, F_TOTAL);
-  fno_tables<<<grid_of(T_RF + T_RI + T_CF + T_CI, 256), 256, 0, F->stream>>>(F->tabs);
+  fno_tables<<<grid_of(T_RF + T_RI + T_CF + T_CI + 2 * T_TCP, 256), 256, 0, F->stream>>>(F->tabs);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(F->m1, 0, sizeof(float) * F_TOTAL, F->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(F->m2, 0, sizeof(float) * F_TOTAL, F->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->dflag, 0, sizeof(int), F->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->stream);
   if (e != cudaSuccess) return fail(e, "FNO init");
   *out = F;
@@ -1426,7 +1589,7 @@ cisor_status cisor_fno_forward(cisor_fno* F, const void* f, int f_per_sample, co
   CISOR_TRY(stage_inputs(F, f, f_per_sample, u_in, nullptr, B));
   CISOR_TRY(fno_forward_core(F, f_per_sample, B, 0, F->ubuf, nullptr));
   CISOR_CUDA(cudaMemcpyAsync(u_sc_out, F->out, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
-  CISOR_CUDA(cudaStreamSynchronize(F->stream));
+  CISOR_TRY(fno_sync(F));
   return fno_leave(F);
 }
 
@@ -1484,7 +1647,7 @@ cisor_status cisor_fno_warm_start(cisor_fno* F, cisor_ctx* c, const void* f, voi
   CISOR_CUDA(cudaStreamWaitEvent(F->stream, c->ev_b, 0));  // the context's incident fields are ready
   CISOR_TRY(fno_forward_core(F, 0, B, 0, c->u_in, F->usc));
   CISOR_CUDA(cudaMemcpyAsync(x0_out, F->usc, sizeof(float2) * (size_t)B * FNN, cudaMemcpyDefault, F->stream));
-  CISOR_CUDA(cudaStreamSynchronize(F->stream));
+  CISOR_TRY(fno_sync(F));
   return fno_leave(F);
 }
 
