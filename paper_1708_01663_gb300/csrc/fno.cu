@@ -15,8 +15,8 @@
 // DFT; Lsyn is (1/128^2) Re of the truncated inverse with weight 2 on ky > 0.
 // Loss: mean over samples of ||out - t|| / ||t||.
 //
-// Every contraction runs on the tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation): the truncated DFTs are small dense GEMMs
+// Every contraction of the network runs on the tensor cores with BF16
+// operands and FP32 accumulation: the truncated DFTs are small dense GEMMs
 // against FP64-built cosine/sine tables (16 of 128 frequencies per axis, so a
 // GEMM reads each value once where a full FFT would transform 8x more), the
 // 1x1 channel mixings, the projection, and the weight gradients (reductions
@@ -24,23 +24,28 @@
 // BF16 values; FP32 master copies and Adam state), so a weight operand is
 // exact; activations and tables are split into BF16 hi + lo parts and a
 // product takes two or three MMAs (about 16 mantissa bits, the accuracy of
-// FP32 arithmetic for these sums).  Only the per-mode 32 x 32 mixing of the
-// forward pass and its transpose in the backward pass (vector x matrix per
-// sample and mode) run on the FP32 pipes.
+// FP32 arithmetic for these sums).  The forward row kernels and the column
+// DFTs (forward and backward) issue fifth-generation tensor-core tiles
+// (tcgen05, accumulators in tensor memory); the lifting and the backward row
+// and projection kernels use warp-level mma.sync tiles.  Only the per-mode
+// 32 x 32 complex mixing (a matrix per mode applied to every sample's vector)
+// and grad R run on the FP32 pipes.
 //
-// A layer is two kernels:
+// A layer is four kernels:
 //   row kernel     (one sample, 2 image rows, all 32 channels): inverse row
 //                  DFT of the mode-mixed spectrum + W v + b, GELU, and the
 //                  forward row DFT of the result for the next layer (or the
 //                  projection after the last layer);
-//   column kernel  (one sample, one ky): column DFT to the 32 kept kx, mode
-//                  mixing with R_l, inverse column DFT.
-// Between them the spectra travel as [B][64 row pairs][16 ky][32 ch][2 rows]
-// complex64 blocks: each row kernel reads and writes one contiguous 8 KB block,
-// each column kernel 64 contiguous 512-byte pieces.  The backward pass mirrors
-// this (row-backward, column-backward, and a per-mode kernel for the spectral
-// weight gradient, a GEMM over the batch), recomputing the projection's
-// hidden layer and the input features instead of storing them.
+//   column DFT     (one sample, 4 ky): the 32 kept kx of every channel;
+//   mode mixing    (one mode, all samples): Y = R_l X;
+//   inverse column DFT (one sample, 4 ky): back to the 128 rows.
+// Between the row and column kernels the spectra travel as [B][64 row pairs]
+// [16 ky][32 ch][2 rows] complex64 blocks (a row kernel reads and writes one
+// contiguous 8 KB block), between the column kernels as [mode][B][32 ch].
+// The backward pass mirrors
+// this (row-backward, column DFT of dT, the mixing's transpose with grad R,
+// inverse column DFT), recomputing the projection's hidden layer and the
+// input features instead of storing them.
 #include <math.h>
 #include <cuda_bf16.h>
 
@@ -73,23 +78,29 @@ constexpr int PART_P = FH * FC + FH + 2 * FH + 2;    // dP1, dc1, dP2, dc2
 constexpr int PART_0 = FC * FIN + FC;                // dW0, db0
 constexpr int PART_MAX = PART_P;
 
-// DFT tables, FP64-built, as BF16 hi / lo pairs laid out so that every MMA
-// fragment register is ONE 32-bit load (the two BF16 values of a register are
-// adjacent along the contraction index) and, from shared memory, conflict-free:
-//   RowF  B operand [kyc][ix], pitch RFP: E(ix, kyc) = cos(2 pi ky ix / 128) (kyc = 2 ky), -sin (kyc = 2 ky + 1)
-//   RowI  B operand [ix][kyc], pitch RIP: the same values, transposed
-//   ColF  A operand [row][k] (64 x 256), pitch CFP: [[Fr, -Fi], [Fi, Fr]], F(kx, iy) = exp(-2 pi j kx' iy / 128)
-//   ColI  A operand [row][k] (256 x 64), pitch CIP: [[Fr, Fi], [-Fi, Fr]] (conj(F) transposed)
-// kx' = kx for kx < 16, kx + 96 otherwise.
-constexpr int RFP = FN + 8, RIP = 2 * FM + 8, CFP = 2 * FN + 8, CIP = 2 * FKX + 8;
-constexpr int T_RF = 2 * FM * RFP, T_RI = FN * RIP, T_CF = 2 * FKX * CFP, T_CI = 2 * FN * CIP;
-constexpr int T_ROW = 2 * (T_RF + T_RI);        // bf16 of the row tables (hi and lo), copied to shared memory
-constexpr int T_COLS = T_ROW + 2 * (T_CF + T_CI);  // + the column tables (read through L1)
-// Row-DFT tables of the tcgen05 row kernel, in the tensor cores' core-matrix layout (tc5.cuh), hi and lo
-// planes of 128 x 32 BF16 each: RowI A operand E^T [128 ix][32 kyc] (LBO 128, SBO 512) and RowF B operand
-// E [32 kyc][128 ix] (LBO 128, SBO 2048).
-constexpr int T_TCP = FN * 2 * FM;                 // BF16 per plane
-constexpr int T_ALL = T_COLS + 4 * T_TCP;
+// DFT tables, FP64-built, as BF16 hi / lo pairs.  E(ix, kyc) = cos(2 pi ky ix / 128) (kyc = 2 ky),
+// -sin (kyc = 2 ky + 1); F(kx, iy) = exp(-2 pi j kx' iy / 128), kx' = kx for kx < 16, kx + 96 otherwise.
+// mma.sync tables (lifting and backward row kernels), laid out so that every fragment register is ONE
+// 32-bit load (the two BF16 values of a register are adjacent along the contraction index) and, from
+// shared memory, conflict-free:
+//   RowF  B operand [kyc][ix], pitch RFP
+//   RowI  B operand [ix][kyc], pitch RIP (the same values, transposed)
+constexpr int RFP = FN + 8, RIP = 2 * FM + 8;
+constexpr int T_RF = 2 * FM * RFP, T_RI = FN * RIP;
+constexpr int T_ROW = 2 * (T_RF + T_RI);  // bf16 of the row tables (hi and lo), copied to shared memory
+// tcgen05 tables in the tensor cores' core-matrix layout (tc5.cuh), each as a hi and a lo plane:
+//   RowI  A operand E^T [128 ix][32 kyc]                (LBO 128, SBO 512)
+//   RowF  B operand E [32 kyc][128 ix]                  (LBO 128, SBO 2048)
+//   ColF  B operand [64 j][256 k], k = 2 iy + p (p: Re / Im of the input), j < 32: Re X(kx = j),
+//         j >= 32: Im X(kx = j - 32); entries Fr, -Fi / Fi, Fr      (LBO 128, SBO 4096)
+//   ColI  B operand [256 j][64 k], j = 2 iy + p (Re / Im of the output), k = 2 kx + p' (Re / Im of the
+//         input): conj(F) as [[Fr, Fi], [-Fi, Fr]] per (iy, kx)    (LBO 128, SBO 1024)
+constexpr int T_TCP = FN * 2 * FM;     // BF16 per plane of the row tables
+constexpr int T_TCF = 2 * FKX * 2 * FN;  // BF16 per plane of the column tables
+constexpr int T_TROW = T_ROW;                  // RowI A hi, lo, RowF B hi, lo
+constexpr int T_TCOLF = T_TROW + 4 * T_TCP;    // ColF B hi, lo
+constexpr int T_TCOLI = T_TCOLF + 2 * T_TCF;   // ColI B hi, lo
+constexpr int T_ALL = T_TCOLI + 2 * T_TCF;
 constexpr int WP = FC + 8;                        // pitch (bf16) of a 32-wide weight row in shared memory
 constexpr int P1TP = FH + 8;                      // pitch (bf16) of P1^T rows
 
@@ -137,21 +148,6 @@ __device__ __forceinline__ void load_b_tab(const uint32_t* tab, int pw, int k0, 
   const uint32_t* row = tab + (n0 + g) * pw + (k0 >> 1) + t;
   b[0] = row[0];
   b[1] = row[4];
-}
-// A fragment (hi and lo) from BF16 tables stored [m][k], pitch pw words, in global memory (read-only path)
-__device__ __forceinline__ FragA load_a_tab(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo, int pw,
-                                            int m0, int k0, int g, int t) {
-  FragA f;
-  const int o0 = (m0 + g) * pw + (k0 >> 1) + t, o1 = o0 + 8 * pw;
-  f.h[0] = __ldg(hi + o0);
-  f.h[1] = __ldg(hi + o1);
-  f.h[2] = __ldg(hi + o0 + 4);
-  f.h[3] = __ldg(hi + o1 + 4);
-  f.l[0] = __ldg(lo + o0);
-  f.l[1] = __ldg(lo + o1);
-  f.l[2] = __ldg(lo + o0 + 4);
-  f.l[3] = __ldg(lo + o1 + 4);
-  return f;
 }
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
@@ -452,7 +448,7 @@ __global__ void __launch_bounds__(NTH, 2) fno_row_tc(const float* __restrict__ v
   float* c1 = reinterpret_cast<float*>(sm + TSM_C1);
   float* p2 = reinterpret_cast<float*>(sm + TSM_P2);
   // tables (RowI A; RowF B, or P1 for the projection), W, bias
-  cta_copy(sm, tabs + T_COLS, (PROJ ? 2 : 4) * TC_TAB);
+  cta_copy(sm, tabs + T_TROW, (PROJ ? 2 : 4) * TC_TAB);
   for (int e = tid; e < FC * FC; e += NTH)
     *reinterpret_cast<__nv_bfloat16*>(sm + TSM_W + core_off(e / FC, e % FC, TC_LBO, TC_SBO)) = wbf[woff + e];
   if (tid < FC) bias[tid] = pm[boff + tid];
@@ -667,160 +663,248 @@ __global__ void __launch_bounds__(NTH, 2) fno_row_tc(const float* __restrict__ v
   if (warp == 0) tmem_dealloc(tmem, NCOL);
 }
 
-// Column kernel, one (ky, sample): X = ColF(T1) over iy to the 32 kept kx; forward: Y = mix_R(X) x w_ky / 128^2,
-// Z = ColI(Y); backward (BWD = 1, T1 = dT): dY = ColF(dT) x w_ky / 128^2, dX = mix_R^H(dY), dU = ColI(dX).
-// Xst (may be null) receives X (forward) or dY (backward) mode-major [mode][B][FC] for the weight gradient.
-constexpr int TSP = FN + 4;   // shared pitch (complex) of a channel's 128 rows
-constexpr int XSP = FC + 1;   // shared pitch (complex) of a mode's 32 channels
-constexpr int SM_COL = (FC * TSP + 2 * FKX * XSP) * 8;
+// ------------------------------------------------------------------ column stage
+// Layer l's spectral convolution along iy, between the row kernels' spectra T
+// ([B][64 row pairs][16 ky][32 c][2] blocks) and Z in the same layout:
+//   X = ColF(T)               the 32 kept kx of the column DFT       (fno_colf_tc, tensor cores)
+//   Y = mix_R(X) w_ky / 128^2 per mode (kx, ky): 32 x 32 complex   (fno_mix, FP32 pipes)
+//   Z = ColI(Y)               inverse column DFT at all 128 iy       (fno_coli_tc, tensor cores)
+// The backward runs the same chain on dT: dY = ColF(dT) w_ky / 128^2,
+// dX = mix_R^H(dY) with grad R = sum_b conj(X) dY in the same kernel
+// (fno_mix_bwd), dU = ColI(dX).  X and dY stay in HBM / L2 between the
+// kernels, mode-major [mode = kx * 16 + ky][B][32 c]: the forward's X is the
+// backward's operand for grad R.
+//
+// The column DFTs are GEMMs with 128 rows = (4 ky) x (32 channels) of one
+// sample, issued as whole tiles by one thread (tc5.cuh), operands in BF16 hi /
+// lo planes (three products, the FP32 accuracy of the other FNO contractions),
+// accumulators in TMEM with row n in lane n: thread (warp w, lane l) owns
+// channel l of ky = 4 g + w % 4, and warps w, w + 4 split its columns.
+constexpr int KY_G = 4;                           // ky per column CTA
+constexpr int CF_SBO = 4096, CI_SBO = 1024;       // 8-row strides of the K = 256 and K = 64 operands
+constexpr int KCF_PA = 128 * 2 * FN * 2;          // bytes of one plane of T [128 n][256 k]
+constexpr int KCI_PA = 128 * 2 * FKX * 2;         // bytes of one plane of Y [128 n][64 k]
+constexpr int KC_PB = T_TCF * 2;                  // bytes of one plane of a column table
+constexpr int SM_COLF = 2 * KCF_PA + 2 * KC_PB;   // 192 KB: one CTA per SM
+constexpr int SM_COLI = 2 * KCI_PA + 2 * KC_PB;   // 96 KB: two CTAs per SM
+__device__ __forceinline__ float ky_scale(int ky) { return (ky ? 2.f : 1.f) / FNN; }
+
+// One thread issues the MMAs, every thread waits (bounded) for their completion: false (and *err set)
+// if the wait gave up anywhere in the CTA.
+__device__ __forceinline__ bool tc_wait_all(uint64_t* mbar, int* err) {
+  const bool ok = mbar_wait(mbar, 0, TC_WAIT);
+  tc_fence_after();
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return false;
+  }
+  return true;
+}
+
+// X[kx][ky][b][c] = sum_iy F(kx, iy) T[iy][ky][b][c] for ky in [4 g, 4 g + 4): D[n][j] = sum_k T[n][k] ColF[j][k]
+// (M 128, N 64, K 256).  BWD: dT in, dY = X w_ky / 128^2 out.  Grid (16 / 4, B).
 template <int BWD>
-__global__ void __launch_bounds__(NTH, 2) fno_col(const float2* __restrict__ Tin,
-                                                  const __nv_bfloat16* __restrict__ tabs,
-                                                  const __nv_bfloat16* __restrict__ wbf, long long roff, int B,
-                                                  float2* __restrict__ Xst, float2* __restrict__ Zout) {
-  extern __shared__ __align__(16) float smem[];
-  float2* ts = reinterpret_cast<float2*>(smem);  // [FC][TSP]: T(iy, c) at c * TSP + iy
-  float2* xs = ts + FC * TSP;                    // [FKX][XSP]
-  float2* ys = xs + FKX * XSP;                   // [FKX][XSP]
-  const int ky = blockIdx.x, b = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  // the block's column: 64 row pairs x 32 channels of 16 bytes ([iyb][ky][c][r] in global memory)
-  for (int i = threadIdx.x; i < NIB * FC; i += NTH) {
-    const int iyb = i / FC, c = i % FC;
-    cp16(ts + c * TSP + iyb * RB, Tin + ((long long)b * NIB + iyb) * BLK + (ky * FC + c) * RB);
+__global__ void __launch_bounds__(NTH, 1) fno_colf_tc(const float2* __restrict__ Tin,
+                                                      const __nv_bfloat16* __restrict__ tabs, int B,
+                                                      float2* __restrict__ Xout, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ky0 = blockIdx.x * KY_G, b = blockIdx.y;
+  cta_copy(sm + 2 * KCF_PA, tabs + T_TCOLF, 2 * KC_PB);
+  // T[n = 32 kyl + c][k = 2 iy + p]: one 16-byte load per (n, row pair) = k 4 iyb .. 4 iyb + 3.  A warp
+  // covers 8 n x 4 row pairs: 128-byte global pieces, 8-byte stores on all 32 banks.
+  const float2* tb = Tin + (long long)b * NIB * BLK + ky0 * FC * RB;
+#pragma unroll 8
+  for (int it = 0; it < NIB * 128 / NTH; ++it) {
+    const int idx = tid + NTH * it;
+    const int n = 8 * ((idx >> 5) & 15) + (idx & 7), iyb = 4 * (idx >> 9) + ((idx >> 3) & 3);
+    const float4 v = __ldg(reinterpret_cast<const float4*>(tb + (long long)iyb * BLK + n * RB));
+    uint2 h, l;
+    split_pair(v.x, v.y, h.x, l.x);
+    split_pair(v.z, v.w, h.y, l.y);
+    const int o = core_off(n, 4 * iyb, TC_LBO, CF_SBO);
+    *reinterpret_cast<uint2*>(sm + o) = h;
+    *reinterpret_cast<uint2*>(sm + KCF_PA + o) = l;
   }
+  if (tid == 0) mbar_init(&mbar);
+  if (warp == 0) tmem_alloc(&tslot, 64);
   cp_wait_all();
+  fence_async_smem();
+  tc_fence_before();
   __syncthreads();
-  const float scale = (ky ? 2.f : 1.f) / FNN;
-  const uint32_t* cfh = reinterpret_cast<const uint32_t*>(tabs + T_ROW);
-  const uint32_t* cfl = cfh + T_CF / 2;
-  const uint32_t* cih = cfl + T_CF / 2;
-  const uint32_t* cil = cih + T_CI / 2;
-  {  // ColF: [Xr; Xi] (64 x 32) = [[Fr, -Fi], [Fi, Fr]] (64 x 256) [Tr; Ti] (256 x 32)
-    const float* tf = reinterpret_cast<const float*>(ts);
-    auto Bt = [&](int k, int c) { return tf[2 * (c * TSP + (k & 127)) + (k >> 7)]; };
-    const int mt = warp & 3, nt0 = (warp >> 2) * 2;
-    float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    FragA a = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 0, g, t);
-#pragma unroll 2
-    for (int ks = 0; ks < 16; ++ks) {  // the next k-step's table fragment is in flight during this one's MMAs
-      const FragA an = load_a_tab(cfh, cfl, CFP / 2, 16 * mt, 16 * ((ks + 1) & 15), g, t);
+  tc_fence_after();
+  const uint32_t tmem = tslot, s0 = smem_addr(sm);
+  if (tid == 0) {
+    const uint32_t id = tc_idesc_bf16(128, 64);
 #pragma unroll
-      for (int j = 0; j < 2; ++j) mma3(d[j], a, load_b(Bt, 16 * ks, 8 * (nt0 + j), g, t));
-      a = an;
+    for (int ks = 0; ks < 2 * FN / 16; ++ks) {
+      const uint32_t ah = s0 + ks * 2 * TC_LBO, al = ah + KCF_PA;
+      const uint32_t bh = s0 + 2 * KCF_PA + ks * 2 * TC_LBO, bl = bh + KC_PB;
+      tc_mma(tmem, tc_desc(ah, TC_LBO, CF_SBO), tc_desc(bh, TC_LBO, CF_SBO), id, ks > 0);
+      tc_mma(tmem, tc_desc(al, TC_LBO, CF_SBO), tc_desc(bh, TC_LBO, CF_SBO), id, 1);
+      tc_mma(tmem, tc_desc(ah, TC_LBO, CF_SBO), tc_desc(bl, TC_LBO, CF_SBO), id, 1);
     }
-    float* xf = reinterpret_cast<float*>(xs);
+    tc_commit(&mbar);
+  }
+  if (tc_wait_all(&mbar, err)) {
+    const int q = warp & 3, h = warp >> 2, ky = ky0 + q;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    const float sc = BWD ? ky_scale(ky) : 1.f;
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int half = 0; half < 2; ++half) {  // kx 16 h + 8 half .. + 7: Re in column kx, Im in column 32 + kx
+      float re[8], im[8];
+      tmem_ld8(tl + 16 * h + 8 * half, re);
+      tmem_ld8(tl + FKX + 16 * h + 8 * half, im);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int row = 16 * mt + g + (e >> 1) * 8, c = 8 * (nt0 + j) + 2 * t + (e & 1);
-        xf[((row & 31) * XSP + c) * 2 + (row >> 5)] = BWD ? d[j][e] * scale : d[j][e];
+      for (int t = 0; t < 8; ++t) {
+        const int kx = 16 * h + 8 * half + t;
+        Xout[((long long)(kx * FM + ky) * B + b) * FC + lane] = make_float2(re[t] * sc, im[t] * sc);
       }
-  }
-  __syncthreads();
-  if (Xst)
-    for (int i = threadIdx.x; i < FKX * FC; i += NTH) {
-      const int kx = i / FC, c = i % FC;
-      Xst[((long long)(kx * FM + ky) * B + b) * FC + c] = xs[kx * XSP + c];
     }
-  // per-mode mixing on the FP32 pipes, warp per kx, lane = output channel
-  for (int kx = warp; kx < FKX; kx += NTH / 32) {
-    const __nv_bfloat162* R = reinterpret_cast<const __nv_bfloat162*>(wbf + roff) + (long long)(kx * FM + ky) * FC * FC;
-    float2 acc = make_float2(0.f, 0.f);
-    if (!BWD) {  // Y[o] = sum_c X[c] R[c][o]
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+// Z[iy][ky][b][o] = sum_kx conj(F(kx, iy)) Y[kx][ky][b][o] for ky in [4 g, 4 g + 4): D[n][j] = sum_k Y[n][k]
+// ColI[j][k] (M 128, N 256, K 64), j = 2 iy + p, written as the row kernels' [iyb][ky][o][2] blocks.
+__global__ void __launch_bounds__(NTH, 2) fno_coli_tc(const float2* __restrict__ Yin,
+                                                      const __nv_bfloat16* __restrict__ tabs, int B,
+                                                      float2* __restrict__ Zout, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ky0 = blockIdx.x * KY_G, b = blockIdx.y;
+  cta_copy(sm + 2 * KCI_PA, tabs + T_TCOLI, 2 * KC_PB);
+  // Y[n = 32 kyl + o][k = 2 kx + p]: a warp covers 8 n x 4 kx (64-byte global pieces, 4-byte stores on
+  // all 32 banks)
 #pragma unroll 8
-      for (int c = 0; c < FC; ++c) acc = c_fma(xs[kx * XSP + c], __bfloat1622float2(R[c * FC + lane]), acc);
-      ys[kx * XSP + lane] = c_scale(acc, scale);
-    } else {     // dX[c] = sum_o conj(R[c][o]) dY[o], lane = c
+  for (int it = 0; it < FKX * 128 / NTH; ++it) {
+    const int idx = tid + NTH * it;
+    const int n = 8 * ((idx >> 5) & 15) + (idx & 7), kx = 4 * (idx >> 9) + ((idx >> 3) & 3);
+    const float2 v = __ldg(Yin + ((long long)(kx * FM + ky0 + (n >> 5)) * B + b) * FC + (n & 31));
+    uint32_t h, l;
+    split_pair(v.x, v.y, h, l);
+    const int o = core_off(n, 2 * kx, TC_LBO, CI_SBO);
+    *reinterpret_cast<uint32_t*>(sm + o) = h;
+    *reinterpret_cast<uint32_t*>(sm + KCI_PA + o) = l;
+  }
+  if (tid == 0) mbar_init(&mbar);
+  if (warp == 0) tmem_alloc(&tslot, 256);
+  cp_wait_all();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot, s0 = smem_addr(sm);
+  if (tid == 0) {
+    const uint32_t id = tc_idesc_bf16(128, 256);
+#pragma unroll
+    for (int ks = 0; ks < 2 * FKX / 16; ++ks) {
+      const uint32_t ah = s0 + ks * 2 * TC_LBO, al = ah + KCI_PA;
+      const uint32_t bh = s0 + 2 * KCI_PA + ks * 2 * TC_LBO, bl = bh + KC_PB;
+      tc_mma(tmem, tc_desc(ah, TC_LBO, CI_SBO), tc_desc(bh, TC_LBO, CI_SBO), id, ks > 0);
+      tc_mma(tmem, tc_desc(al, TC_LBO, CI_SBO), tc_desc(bh, TC_LBO, CI_SBO), id, 1);
+      tc_mma(tmem, tc_desc(ah, TC_LBO, CI_SBO), tc_desc(bl, TC_LBO, CI_SBO), id, 1);
+    }
+    tc_commit(&mbar);
+  }
+  if (tc_wait_all(&mbar, err)) {
+    const int q = warp & 3, h = warp >> 2, ky = ky0 + q;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    float4* zb = reinterpret_cast<float4*>(Zout + (long long)b * NIB * BLK + (ky * FC + lane) * RB);
+#pragma unroll 4
+    for (int m = 0; m < 16; ++m) {  // columns 128 h + 8 m ..: iy 64 h + 4 m .. + 3 = row pairs 32 h + 2 m, + 1
+      float d[8];
+      tmem_ld8(tl + 128 * h + 8 * m, d);
+      const int iyb = 32 * h + 2 * m;
+      zb[(long long)iyb * (BLK / 2)] = make_float4(d[0], d[1], d[2], d[3]);
+      zb[(long long)(iyb + 1) * (BLK / 2)] = make_float4(d[4], d[5], d[6], d[7]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// Y[m][b][o] = w_ky / 128^2 sum_c X[m][b][c] R[m][c][o], one CTA per mode m = (kx, ky), samples in chunks
+// of 32: thread (warp w, lane o) forms samples w, w + 8, w + 16, w + 24 of the chunk.
+constexpr int MIXP = FC + 1;  // shared pitch (complex) of a 32-wide row
+__global__ void __launch_bounds__(NTH) fno_mix(const float2* __restrict__ X, const __nv_bfloat16* __restrict__ wbf,
+                                               long long roff, int B, float2* __restrict__ Y) {
+  __shared__ float2 rs[FC * MIXP], xs[32 * MIXP];
+  const int m = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const __nv_bfloat162* R = reinterpret_cast<const __nv_bfloat162*>(wbf + roff) + (long long)m * FC * FC;
+  for (int e = threadIdx.x; e < FC * FC; e += NTH) rs[(e / FC) * MIXP + e % FC] = __bfloat1622float2(R[e]);
+  const float sc = ky_scale(m % FM);
+  for (int b0 = 0; b0 < B; b0 += 32) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * FC; e += NTH) {
+      const int bb = b0 + e / FC;
+      xs[(e / FC) * MIXP + e % FC] = bb < B ? X[((long long)m * B + bb) * FC + e % FC] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 acc[4] = {};
 #pragma unroll 8
-      for (int o = 0; o < FC; ++o) acc = c_cjfma(__bfloat1622float2(R[lane * FC + o]), xs[kx * XSP + o], acc);
-      ys[kx * XSP + lane] = acc;
-    }
-  }
-  __syncthreads();
-  {  // ColI: [Zr; Zi] (256 x 32) = [[Fr, Fi], [-Fi, Fr]] (256 x 64) [Yr; Yi] (64 x 32)
-    const float* yf = reinterpret_cast<const float*>(ys);
-    auto By = [&](int k, int o) { return yf[2 * ((k & 31) * XSP + o) + (k >> 5)]; };
-    float* zf = reinterpret_cast<float*>(ts);
-    float d[2][4][4];
+    for (int c = 0; c < FC; ++c) {
+      const float2 r = rs[c * MIXP + lane];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) d[h][j][0] = d[h][j][1] = d[h][j][2] = d[h][j][3] = 0.f;
-    FragA a0 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp), 0, g, t);
-    FragA a1 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + 1), 0, g, t);
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      FragB bq[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bq[j] = load_b(By, 16 * ks, 8 * j, g, t);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) mma3(d[0][j], a0, bq[j]);
-      if (ks < 3) a0 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp), 16 * (ks + 1), g, t);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) mma3(d[1][j], a1, bq[j]);
-      if (ks < 3) a1 = load_a_tab(cih, cil, CIP / 2, 16 * (2 * warp + 1), 16 * (ks + 1), g, t);
+      for (int i = 0; i < 4; ++i) acc[i] = c_fma(xs[(warp + 8 * i) * MIXP + c], r, acc[i]);
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int row = 16 * (2 * warp + h) + g + (e >> 1) * 8, o = 8 * j + 2 * t + (e & 1);
-          zf[2 * (o * TSP + (row & 127)) + (row >> 7)] = d[h][j][e];
-        }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NIB * FC; i += NTH) {
-    const int iyb = i / FC, c = i % FC;
-    *reinterpret_cast<float4*>(Zout + ((long long)b * NIB + iyb) * BLK + (ky * FC + c) * RB) =
-        *reinterpret_cast<const float4*>(ts + c * TSP + iyb * RB);
+    for (int i = 0; i < 4; ++i) {
+      const int bb = b0 + warp + 8 * i;
+      if (bb < B) Y[((long long)m * B + bb) * FC + lane] = c_scale(acc[i], sc);
+    }
   }
 }
 
-// ------------------------------------------------------------------ backward kernels
-// grad R_l[m][c][o] = sum_b conj(X[m][b][c]) dY[m][b][o], one CTA per mode:
-// real GEMM M = 32 (c), N = 64 (Re / Im of o), K = 64 per chunk of 32 samples.
-__global__ void __launch_bounds__(NTH) fno_dR(const float2* __restrict__ Xst, const float2* __restrict__ dYst, int B,
-                                             float* __restrict__ grad) {
-  __shared__ float2 xs[32 * XSP], gs[32 * XSP];
-  const int m = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const int mt = warp & 1, nt0 = (warp >> 1) * 2;
-  float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  const float* xf = reinterpret_cast<const float*>(xs);
-  const float* gf = reinterpret_cast<const float*>(gs);
-  auto A = [&](int c, int k) { return xf[2 * ((k & 31) * XSP + c) + (k >> 5)]; };
-  auto Bg = [&](int k, int n) {
-    const int o = n & 31, bb = k & 31;
-    const float re = gf[2 * (bb * XSP + o)], im = gf[2 * (bb * XSP + o) + 1];
-    return n < 32 ? (k < 32 ? re : im) : (k < 32 ? im : -re);
-  };
+// Backward of the mixing for mode m: dX[b][c] = sum_o conj(R[c][o]) dY[b][o] (thread: lane c, samples w + 8 i)
+// and grad R[m][c][o] = sum_b conj(X[b][c]) dY[b][o] (thread: rows c = w + 8 i, lane o), the batch summed in
+// one CTA in sample order (deterministic), written as (Re, Im) pairs.
+__global__ void __launch_bounds__(NTH) fno_mix_bwd(const float2* __restrict__ X, const float2* __restrict__ dY,
+                                                   const __nv_bfloat16* __restrict__ wbf, long long roff, int B,
+                                                   float2* __restrict__ dX, float* __restrict__ gradR) {
+  __shared__ float2 rs[FC * MIXP], xs[32 * MIXP], gs[32 * MIXP];
+  const int m = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const __nv_bfloat162* R = reinterpret_cast<const __nv_bfloat162*>(wbf + roff) + (long long)m * FC * FC;
+  for (int e = threadIdx.x; e < FC * FC; e += NTH) rs[(e / FC) * MIXP + e % FC] = __bfloat1622float2(R[e]);
+  float2 gr[4] = {};
   for (int b0 = 0; b0 < B; b0 += 32) {
     __syncthreads();
-    for (int i = threadIdx.x; i < 32 * FC; i += NTH) {
-      const int bb = b0 + i / FC, c = i % FC;
-      const long long src = ((long long)m * B + bb) * FC + c;
-      xs[(i / FC) * XSP + c] = bb < B ? Xst[src] : make_float2(0.f, 0.f);
-      gs[(i / FC) * XSP + c] = bb < B ? dYst[src] : make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < 32 * FC; e += NTH) {
+      const int bb = b0 + e / FC;
+      const long long src = ((long long)m * B + bb) * FC + e % FC;
+      xs[(e / FC) * MIXP + e % FC] = bb < B ? X[src] : make_float2(0.f, 0.f);
+      gs[(e / FC) * MIXP + e % FC] = bb < B ? dY[src] : make_float2(0.f, 0.f);
     }
     __syncthreads();
+    float2 acc[4] = {};
+#pragma unroll 8
+    for (int o = 0; o < FC; ++o) {
+      const float2 r = rs[lane * MIXP + o];
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const FragA a = load_a(A, 16 * mt, 16 * ks, g, t);
+      for (int i = 0; i < 4; ++i) acc[i] = c_cjfma(r, gs[(warp + 8 * i) * MIXP + o], acc[i]);
+    }
 #pragma unroll
-      for (int j = 0; j < 2; ++j) mma3(d[j], a, load_b(Bg, 16 * ks, 8 * (nt0 + j), g, t));
+    for (int i = 0; i < 4; ++i) {
+      const int bb = b0 + warp + 8 * i;
+      if (bb < B) dX[((long long)m * B + bb) * FC + lane] = acc[i];
+    }
+    const int nb = B - b0 < 32 ? B - b0 : 32;
+    for (int bb = 0; bb < nb; ++bb) {
+      const float2 g = gs[bb * MIXP + lane];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) gr[i] = c_cjfma(xs[bb * MIXP + warp + 8 * i], g, gr[i]);
     }
   }
+  float2* out = reinterpret_cast<float2*>(gradR) + (long long)m * FC * FC;
 #pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int c = 16 * mt + g + (e >> 1) * 8, n = 8 * (nt0 + j) + 2 * t + (e & 1);
-      grad[((long long)m * FC * FC + c * FC + (n & 31)) * 2 + (n >> 5)] = d[j][e];
-    }
+  for (int i = 0; i < 4; ++i) out[(warp + 8 * i) * FC + lane] = gr[i];
 }
 
 // Layer l backward, persistent over (sample, row block) items:
@@ -1113,12 +1197,27 @@ __global__ void __launch_bounds__(NTH, 2) fno_lift_bwd(const float* __restrict__
   if ((threadIdx.x & 7) == 0) pp[FC * FIN + (threadIdx.x >> 3)] = db;
 }
 
-__global__ void fno_reduce(const float* __restrict__ part, int nparts, int count, float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+// out[i] = sum_p part[p][i] in a fixed order (deterministic): a CTA takes 32 consecutive i (lanes, coalesced),
+// its RED_W warps sum the partials p = w, w + RED_W, ... and warp 0 adds the RED_W sums in warp order.
+constexpr int RED_W = 16;
+__global__ void __launch_bounds__(32 * RED_W) fno_reduce(const float* __restrict__ part, int nparts, int count,
+                                                        float* __restrict__ out) {
+  __shared__ float sw[RED_W][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int p = 0; p < nparts; ++p) s += part[(long long)p * count + i];
-  out[i] = s;
+  if (i < count) {
+#pragma unroll 4
+    for (int p = warp; p < nparts; p += RED_W) s += part[(long long)p * count + i];
+  }
+  sw[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < count) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < RED_W; ++w) t += sw[w][lane];
+    out[i] = t;
+  }
 }
 
 // Per-sample relative L2 loss and its gradient (planar [B][2][FNN]); one CTA per sample.
@@ -1185,32 +1284,28 @@ __global__ void fno_tables(__nv_bfloat16* __restrict__ tabs) {
     if (kyc < 2 * FM) v = row_entry(ix, kyc);
     hi = tabs + 2 * T_RF + j;
     lo = hi + T_RI;
-  } else if (i < T_RF + T_RI + T_CF) {  // ColF [row][k]: [[Fr, -Fi], [Fi, Fr]]
-    const int j = i - T_RF - T_RI, row = j / CFP, k = j % CFP;
-    if (k < 2 * FN) {
-      const double2 F = col_entry(row & 31, k & 127);
-      v = (row < 32) ? ((k < FN) ? F.x : -F.y) : ((k < FN) ? F.y : F.x);
-    }
-    hi = tabs + T_ROW + j;
-    lo = hi + T_CF;
-  } else if (i < T_RF + T_RI + T_CF + T_CI) {  // ColI [row][k]: [[Fr, Fi], [-Fi, Fr]]
-    const int j = i - T_RF - T_RI - T_CF, row = j / CIP, k = j % CIP;
-    if (k < 2 * FKX) {
-      const double2 F = col_entry(k & 31, row & 127);
-      v = (row < FN) ? ((k < FKX) ? F.x : F.y) : ((k < FKX) ? -F.y : F.x);
-    }
-    hi = tabs + T_ROW + 2 * T_CF + j;
-    lo = hi + T_CI;
-  } else if (i < T_RF + T_RI + T_CF + T_CI + T_TCP) {  // tcgen05 RowI A: row ix, K = kyc
-    const int j = i - (T_RF + T_RI + T_CF + T_CI), ix = j / (2 * FM), kyc = j % (2 * FM);
+  } else if (i < T_RF + T_RI + T_TCP) {  // tcgen05 RowI A: row ix, K = kyc
+    const int j = i - (T_RF + T_RI), ix = j / (2 * FM), kyc = j % (2 * FM);
     v = row_entry(ix, kyc);
-    hi = tabs + T_COLS + core_off(ix, kyc, 128, 512) / 2;
+    hi = tabs + T_TROW + core_off(ix, kyc, 128, 512) / 2;
     lo = hi + T_TCP;
-  } else if (i < T_RF + T_RI + T_CF + T_CI + 2 * T_TCP) {  // tcgen05 RowF B: row kyc, K = ix
-    const int j = i - (T_RF + T_RI + T_CF + T_CI + T_TCP), kyc = j / FN, ix = j % FN;
+  } else if (i < T_RF + T_RI + 2 * T_TCP) {  // tcgen05 RowF B: row kyc, K = ix
+    const int j = i - (T_RF + T_RI + T_TCP), kyc = j / FN, ix = j % FN;
     v = row_entry(ix, kyc);
-    hi = tabs + T_COLS + 2 * T_TCP + core_off(kyc, ix, 128, 2048) / 2;
+    hi = tabs + T_TROW + 2 * T_TCP + core_off(kyc, ix, 128, 2048) / 2;
     lo = hi + T_TCP;
+  } else if (i < T_RF + T_RI + 2 * T_TCP + T_TCF) {  // tcgen05 ColF B: row j, K = 2 iy + p
+    const int e = i - (T_RF + T_RI + 2 * T_TCP), j = e / (2 * FN), k = e % (2 * FN);
+    const double2 F = col_entry(j & 31, k >> 1);
+    v = (j < FKX) ? ((k & 1) ? -F.y : F.x) : ((k & 1) ? F.x : F.y);
+    hi = tabs + T_TCOLF + core_off(j, k, 128, 4096) / 2;
+    lo = hi + T_TCF;
+  } else if (i < T_RF + T_RI + 2 * T_TCP + 2 * T_TCF) {  // tcgen05 ColI B: row j = 2 iy + p, K = 2 kx + p'
+    const int e = i - (T_RF + T_RI + 2 * T_TCP + T_TCF), j = e / (2 * FKX), k = e % (2 * FKX);
+    const double2 F = col_entry(k >> 1, j >> 1);
+    v = (j & 1) ? ((k & 1) ? F.x : -F.y) : ((k & 1) ? F.y : F.x);
+    hi = tabs + T_TCOLI + core_off(j, k, 128, 1024) / 2;
+    lo = hi + T_TCF;
   } else {
     return;
   }
@@ -1291,6 +1386,7 @@ struct cisor_fno {
   // activations [max_batch, ...]
   float *v[FL + 1], *pre[FL], *dout, *dvA, *dvB, *loss;
   float2 *Xst[FL], *dYst, *T1, *Zb, *out, *fbuf, *ubuf, *tbuf, *usc;
+  float2 *Xsc, *Ysc;  // column-stage intermediates [mode][B][FC]: X of an inference pass / dX, and Y
   float* h_loss;
   int* dflag;   // set by a kernel whose bounded wait on the tensor cores gave up
   int* h_flag;  // pinned copy of dflag
@@ -1315,8 +1411,9 @@ cisor_status fno_kernel_attrs() {
   CISOR_CUDA(cudaFuncSetAttribute(fno_lift_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_LIFT));
   CISOR_CUDA(cudaFuncSetAttribute(fno_row_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW_TC));
   CISOR_CUDA(cudaFuncSetAttribute(fno_row_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_ROW_TC));
-  CISOR_CUDA(cudaFuncSetAttribute(fno_col<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
-  CISOR_CUDA(cudaFuncSetAttribute(fno_col<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COL));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_colf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COLF));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_colf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COLF));
+  CISOR_CUDA(cudaFuncSetAttribute(fno_coli_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_COLI));
   CISOR_CUDA(cudaFuncSetAttribute(fno_row_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_RBWD));
   CISOR_CUDA(cudaFuncSetAttribute(fno_proj_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_PBWD));
   CISOR_CUDA(cudaFuncSetAttribute(fno_lift_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_LBWD));
@@ -1328,12 +1425,17 @@ cisor_status fno_kernel_attrs() {
 // null) receives the warm start u_in (1 + e) for u_in = xin.
 cisor_status fno_forward_core(cisor_fno* F, int fps, int B, int train, const float2* xin, float2* x0) {
   cudaStream_t s = F->stream;
-  const dim3 grow(NIB, B), gcol(FM, B);
+  const dim3 grow(NIB, B), gcol(FM / KY_G, B);
   const int gper = (int)((long long)B * NIB < F->grid_bwd ? (long long)B * NIB : F->grid_bwd);
   fno_lift_fwd<<<grow, NTH, SM_LIFT, s>>>(F->fbuf, fps, xin, F->wbf, F->pm, F->tabs, F->v[0], F->T1);
   CISOR_CUDA(cudaGetLastError());
   for (int l = 0; l < FL; ++l) {
-    fno_col<0><<<gcol, NTH, SM_COL, s>>>(F->T1, F->tabs, F->wbf, f_R(l), B, train ? F->Xst[l] : nullptr, F->Zb);
+    float2* X = train ? F->Xst[l] : F->Xsc;
+    fno_colf_tc<0><<<gcol, NTH, SM_COLF, s>>>(F->T1, F->tabs, B, X, F->dflag);
+    CISOR_CUDA(cudaGetLastError());
+    fno_mix<<<FMODES, NTH, 0, s>>>(X, F->wbf, f_R(l), B, F->Ysc);
+    CISOR_CUDA(cudaGetLastError());
+    fno_coli_tc<<<gcol, NTH, SM_COLI, s>>>(F->Ysc, F->tabs, B, F->Zb, F->dflag);
     CISOR_CUDA(cudaGetLastError());
     const int last = l == FL - 1;
     float* pre = train ? F->pre[l] : nullptr;
@@ -1354,12 +1456,12 @@ cisor_status fno_backward_core(cisor_fno* F, int fps, int B) {
   cudaStream_t s = F->stream;
   const int G = F->grid_bwd;
   const int Gi = (int)((long long)B * NIB < G ? (long long)B * NIB : G);
-  const dim3 gcol(FM, B);
+  const dim3 gcol(FM / KY_G, B);
   fno_loss<<<B, 256, 0, s>>>(F->out, F->tbuf, B, F->dout, F->loss);
   CISOR_CUDA(cudaGetLastError());
   fno_proj_bwd<<<Gi, NTH, SM_PBWD, s>>>(F->v[FL], F->dout, F->wbf, F->pm, B, F->dvA, F->part);
   CISOR_CUDA(cudaGetLastError());
-  fno_reduce<<<grid_of(PART_P, 256), 256, 0, s>>>(F->part, Gi, PART_P, F->grad + F_P1);
+  fno_reduce<<<grid_of(PART_P, 32), 32 * RED_W, 0, s>>>(F->part, Gi, PART_P, F->grad + F_P1);
   CISOR_CUDA(cudaGetLastError());
   float* dv = F->dvA;
   float* dvn = F->dvB;
@@ -1367,11 +1469,13 @@ cisor_status fno_backward_core(cisor_fno* F, int fps, int B) {
     fno_row_bwd<<<Gi, NTH, SM_RBWD, s>>>(dv, l == FL - 1 ? nullptr : F->Zb, F->pre[l], F->v[l], F->wbf, f_W(l),
                                          F->tabs, B, l < FL - 1, dvn, F->T1, F->part);
     CISOR_CUDA(cudaGetLastError());
-    fno_reduce<<<grid_of(PART_W, 256), 256, 0, s>>>(F->part, Gi, PART_W, F->grad + f_W(l));
+    fno_reduce<<<grid_of(PART_W, 32), 32 * RED_W, 0, s>>>(F->part, Gi, PART_W, F->grad + f_W(l));
     CISOR_CUDA(cudaGetLastError());
-    fno_col<1><<<gcol, NTH, SM_COL, s>>>(F->T1, F->tabs, F->wbf, f_R(l), B, F->dYst, F->Zb);
+    fno_colf_tc<1><<<gcol, NTH, SM_COLF, s>>>(F->T1, F->tabs, B, F->dYst, F->dflag);
     CISOR_CUDA(cudaGetLastError());
-    fno_dR<<<FMODES, NTH, 0, s>>>(F->Xst[l], F->dYst, B, F->grad + f_R(l));
+    fno_mix_bwd<<<FMODES, NTH, 0, s>>>(F->Xst[l], F->dYst, F->wbf, f_R(l), B, F->Xsc, F->grad + f_R(l));
+    CISOR_CUDA(cudaGetLastError());
+    fno_coli_tc<<<gcol, NTH, SM_COLI, s>>>(F->Xsc, F->tabs, B, F->Zb, F->dflag);
     CISOR_CUDA(cudaGetLastError());
     float* tmp = dv;
     dv = dvn;
@@ -1379,7 +1483,7 @@ cisor_status fno_backward_core(cisor_fno* F, int fps, int B) {
   }
   fno_lift_bwd<<<Gi, NTH, SM_LBWD, s>>>(dv, F->Zb, F->fbuf, fps, F->ubuf, F->tabs, B, F->part);
   CISOR_CUDA(cudaGetLastError());
-  fno_reduce<<<grid_of(PART_0, 256), 256, 0, s>>>(F->part, Gi, PART_0, F->grad + F_W0);
+  fno_reduce<<<grid_of(PART_0, 32), 32 * RED_W, 0, s>>>(F->part, Gi, PART_0, F->grad + F_W0);
   CISOR_CUDA(cudaGetLastError());
   return CISOR_OK;
 }
@@ -1426,7 +1530,8 @@ void fno_free(cisor_fno* F) {
   if (!F) return;
   if (F->stream) cudaStreamSynchronize(F->stream);
   void* d[] = {F->pm,  F->grad, F->m1,   F->m2,  F->part, F->wbf,  F->tabs, F->dout, F->dvA,
-               F->dvB, F->loss, F->dYst, F->T1,  F->Zb,   F->out,  F->fbuf, F->ubuf, F->tbuf, F->usc};
+               F->dvB, F->loss, F->dYst, F->T1,  F->Zb,   F->out,  F->fbuf, F->ubuf, F->tbuf, F->usc,
+               F->Xsc, F->Ysc};
   for (void* p : d)
     if (p) cudaFree(p);
   for (int l = 0; l <= FL; ++l)
@@ -1494,6 +1599,8 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
                 {(void**)&F->dvB, act},
                 {(void**)&F->loss, sizeof(float) * max_batch},
                 {(void**)&F->dYst, md},
+                {(void**)&F->Xsc, md},
+                {(void**)&F->Ysc, md},
                 {(void**)&F->T1, spec},
                 {(void**)&F->Zb, spec},
                 {(void**)&F->out, fld},
@@ -1521,7 +1628,7 @@ cisor_status cisor_fno_create(cisor_fno** out, int max_batch, unsigned long long
   }
   fno_init<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F_TOTAL, seed);
   fno_to_bf16<<<grid_of(F_TOTAL, 256), 256, 0, F->stream>>>(F->pm, F->wbf, F_TOTAL);
-  fno_tables<<<grid_of(T_RF + T_RI + T_CF + T_CI + 2 * T_TCP, 256), 256, 0, F->stream>>>(F->tabs);
+  fno_tables<<<grid_of(T_RF + T_RI + 2 * T_TCP + 2 * T_TCF, 256), 256, 0, F->stream>>>(F->tabs);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(F->m1, 0, sizeof(float) * F_TOTAL, F->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(F->m2, 0, sizeof(float) * F_TOTAL, F->stream);
