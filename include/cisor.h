@@ -350,7 +350,12 @@ cisor_status cisor_batch_grad(cisor_batch* b, const void* const* f, const void* 
  * solve (x0_mode 1), which still stops on the true residual.  Parameter
  * arrays are [cisor_fno_num_params] floats in the layout W0 [32x8], b0 [32],
  * per layer l: R_l [32 kx][16 ky][32 in][32 out] complex, W_l [32x32], b_l
- * [32]; then P1 [128x32], c1 [128], P2 [2x128], c2 [2]. */
+ * [32]; then P1 [128x32], c1 [128], P2 [2x128], c2 [2].
+ * Errors: the calls that run the network (forward, loss_grad, train_step,
+ * warm_start) synchronise the network's stream before they return; if a
+ * kernel's bounded wait on its tensor-core operations gave up, the call
+ * returns CISOR_ERR_CUDA ("a wait on the tensor cores timed out") and its
+ * outputs are invalid; the context stays usable. */
 typedef struct cisor_fno cisor_fno;
 
 /* Seeded random initialisation; max_batch (1..256) samples per call. */

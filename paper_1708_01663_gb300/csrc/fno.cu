@@ -558,12 +558,14 @@ __global__ void __launch_bounds__(NTH, 2) fno_row_tc(const float* __restrict__ v
     if (!wait_mma()) break;
     // epilogue: pre = D + b (to global when training), v_{l+1} = act(pre) to global, staged as the next A
     float v[FC];
+    tmem_ld32(tl + 32 * r, v);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float d[8];
-      tmem_ld8(tl + 32 * r + 8 * j, d);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[8 * j + k] = d[k] + bias[8 * j + k];
+    for (int j = 0; j < FC / 4; ++j) {
+      const float4 bj = reinterpret_cast<const float4*>(bias)[j];
+      v[4 * j] += bj.x;
+      v[4 * j + 1] += bj.y;
+      v[4 * j + 2] += bj.z;
+      v[4 * j + 3] += bj.w;
     }
     {
       const long long g0 = gbase + (long long)r * FN + ix;
@@ -621,29 +623,29 @@ __global__ void __launch_bounds__(NTH, 2) fno_row_tc(const float* __restrict__ v
     if (!PROJ) {  // T1 block [ky][c][r] from rows 32 r + c (lanes 16 q + m), columns split by warp half
       float2* dst = T1 + ((long long)b * NIB + iyb) * BLK;
       const int rr = 16 * q4 + lane;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        float d[8];
-        tmem_ld8(tl + 64 + 16 * r + 8 * j, d);
-        if (lane < 16)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int ky = 8 * r + 4 * j + k;
-            dst[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[2 * k], d[2 * k + 1]);
-          }
-      }
-    } else {  // out = P2 GELU(z + c1) + c2 for this thread's pixel; warm start x0 = u_in (1 + out)
-      float o0 = c20, o1 = c21;
-#pragma unroll 2
-      for (int j = 0; j < FH / 8; ++j) {
-        float d[8];
-        tmem_ld8(tl + 128 * r + 8 * j, d);
+      float d[16];
+      tmem_ld16(tl + 64 + 16 * r, d);
+      if (lane < 16)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int hid = 8 * j + k;
-          const float hv = gelu_f(d[k] + c1[hid]);
-          o0 += p2[hid] * hv;
-          o1 += p2[FH + hid] * hv;
+          const int ky = 8 * r + k;
+          dst[(ky * FC + (rr & 31)) * RB + (rr >> 5)] = make_float2(d[2 * k], d[2 * k + 1]);
+        }
+    } else {  // out = P2 GELU(z + c1) + c2 for this thread's pixel; warm start x0 = u_in (1 + out)
+      float o0 = c20, o1 = c21;
+      const float4 *c14 = reinterpret_cast<const float4*>(c1), *p204 = reinterpret_cast<const float4*>(p2),
+                   *p214 = reinterpret_cast<const float4*>(p2 + FH);
+#pragma unroll 1
+      for (int j = 0; j < FH / 32; ++j) {
+        float d[32];
+        tmem_ld32(tl + 128 * r + 32 * j, d);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float4 cc = c14[8 * j + k], q0 = p204[8 * j + k], q1 = p214[8 * j + k];
+          const float h0 = gelu_f(d[4 * k] + cc.x), h1 = gelu_f(d[4 * k + 1] + cc.y);
+          const float h2 = gelu_f(d[4 * k + 2] + cc.z), h3 = gelu_f(d[4 * k + 3] + cc.w);
+          o0 += q0.x * h0 + q0.y * h1 + q0.z * h2 + q0.w * h3;
+          o1 += q1.x * h0 + q1.y * h1 + q1.z * h2 + q1.w * h3;
         }
       }
       const long long pix = (long long)b * FNN + pix0 + (long long)r * FN + ix;
