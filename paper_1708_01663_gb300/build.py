@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcisor.so")
-SOURCES = ["tables.cu", "conv.cu", "conv_cluster.cu", "solver.cu", "sense.cu", "tv.cu", "api.cu", "static_scratch.cu", "batch.cu", "fno.cu",
+SOURCES = ["tables.cu", "conv.cu", "conv_cluster.cu", "solver.cu", "sense.cu", "sense_tc.cu", "tv.cu", "api.cu", "static_scratch.cu", "batch.cu", "fno.cu",
            "vector.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

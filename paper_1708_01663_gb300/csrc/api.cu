@@ -65,6 +65,7 @@ struct Call {
     return CISOR_OK;
   }
   cisor_status leave() {
+    CISOR_TRY(sense_tc_check(c));
     CISOR_CUDA(cudaEventRecord(c->ev_b, c->stream));
     CISOR_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_b, 0));
     if (host_out) CISOR_CUDA(cudaStreamSynchronize(c->stream));
@@ -191,11 +192,13 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf, c->f_ck};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf, c->f_ck, c->Ht,
+                 c->tc_err};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
   if (c->h_dsum) cudaFreeHost(c->h_dsum);
+  if (c->h_tc_err) cudaFreeHost(c->h_tc_err);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -316,6 +319,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   } while (0)
   {
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
@@ -350,7 +354,20 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   ALLOC(c->Y, TM);
   ALLOC(c->w, TM);
   ALLOC(c->yobs, TM);
-  ALLOC(c->sense_part, TM * c->ksplit);
+  {
+    int ks = c->ksplit;
+    if (sense_tc_ok(c)) {  // tensor-core sensing: the transposed matrix, the timeout flag, its split-K partials
+      ALLOC(c->Ht, (size_t)c->M * c->Nf * sizeof(float2));
+      ALLOC(c->tc_err, sizeof(int));
+      cudaError_t e = cudaMemset(c->tc_err, 0, sizeof(int));
+      if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset", __FILE__, __LINE__));
+      st = sense_tc_setup(c);
+      if (st != CISOR_OK) return fail(st);
+      const int s = sense_tc_splits(c, nullptr);
+      if (s > ks) ks = s;
+    }
+    ALLOC(c->sense_part, TM * ks);
+  }
   ALLOC(c->part, sizeof(float) * 2 * DOT_SLOTS * (size_t)c->T * c->nblk * c->ncomp);
   if (c->ncomp == 3) ALLOC(c->vbuf, TN);
   ALLOC(c->scal, sizeof(double) * 2 * SC_STRIDE * (size_t)c->T);
@@ -369,6 +386,7 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   {
     cudaError_t e = cudaMallocHost((void**)&c->h_active, sizeof(int) * c->T);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_dsum, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_tc_err, sizeof(int));
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__));
   }
   st = conv_init(P);

@@ -119,6 +119,12 @@ struct cisor_ctx {
   unsigned char* rx_mask;        // [T, M] active receivers (NULL: all), set by cisor_set_rx_mask
   float2* sense_part;            // [ksplit, T, M]
   int ksplit;
+  float2* Ht;                    // [Nf, M] transposed sensing matrix of the tensor-core adjoint (null: FP32 GEMMs)
+  int* tc_err;                   // set by a sensing kernel whose bounded wait on the tensor cores gave up
+  int* h_tc_err;                 // pinned copy of tc_err
+  bool tc_used;                  // a tensor-core sensing kernel ran in the current call
+  int sms;                       // multiprocessors of the device
+  int sense_tc_occ;              // resident CTAs per SM of the tensor-core forward sensing kernel
   float* part;     // [T, nblk, DOT_SLOTS] float2
   int nblk;        // dot partials per transmitter
   double* scal;    // [T, SC_STRIDE] double2
@@ -309,6 +315,14 @@ cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float
 cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, const float2* y, float2* Z, float2* w,
                             int ntx);
 cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx);
+// tensor-core sensing GEMMs (sense_tc.cu): available when sense_tc_ok; sense_tc_prepare builds Ht from H
+bool sense_tc_ok(const cisor_ctx* c);
+int sense_tc_splits(const cisor_ctx* c, long long* KS);
+cisor_status sense_tc_setup(cisor_ctx* c);
+cisor_status sense_tc_prepare(cisor_ctx* c);
+cisor_status sense_tc_forward(cisor_ctx* c, const float2* f, const float2* u, int ntx, int* splits);
+cisor_status sense_tc_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx);
+cisor_status sense_tc_check(cisor_ctx* c);
 cisor_status grad_assemble(cisor_ctx* c, const float2* u, const float2* gz, const float2* s, double gamma,
                            float2* grad, float2* zstep, int ntx);
 cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, double gamma, float2* z);

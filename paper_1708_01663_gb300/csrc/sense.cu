@@ -8,7 +8,10 @@
 //  sense_adjoint : z_t = H^H w_t and b_t = conj(f) .* z_t        (Eq. 13 right-hand side)
 //  grad_assemble : g = sum_t conj(u_t) .* (z_t + G^H v_t)        (Eq. 12 before Re)
 //                  and the gradient step s - gamma grad D        (Eq. 9 argument)
-// The GEMMs run on the FP32 pipes: complex64 parity (1e-4) rules out TF32.
+// The GEMMs run on the tensor cores (TF32 hi / lo products, sense_tc.cu) where
+// the sizes allow it (T <= 128, even M and field length) and otherwise on the
+// FP32 pipes with the tiles below; a single TF32 product would break the 1e-5
+// sensing parity.
 #include <math.h>
 
 #include "common.cuh"
@@ -109,18 +112,39 @@ __global__ void __launch_bounds__(256, 2) sense_fwd_kernel(const float2* __restr
     }
 }
 
-__global__ void __launch_bounds__(256) sense_reduce_kernel(const float2* __restrict__ part, int ks, int T, int M,
-                                                           const float2* __restrict__ y, float2* __restrict__ Z,
-                                                           float2* __restrict__ w, double* __restrict__ dsum,
-                                                           const unsigned char* __restrict__ mask) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double d = 0.0;
-  if (idx < T * M) {
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < ks; ++k) {
-      const float2 p = part[(long long)k * T * M + idx];
+// Z = sum of the ks split-K partials in FP64, w = Z - y (0 at receivers a transmitter does not record), and
+// D += 1/2 sum |w|^2.  A CTA takes 32 consecutive entries (lanes, coalesced); its 8 warps sum the partials
+// k = w, w + 8, ... and warp 0 adds the 8 sums in warp order (the same order every call).
+constexpr int RED_WARPS = 8;
+__global__ void __launch_bounds__(32 * RED_WARPS) sense_reduce_kernel(const float2* __restrict__ part, int ks, int T,
+                                                                     int M, const float2* __restrict__ y,
+                                                                     float2* __restrict__ Z, float2* __restrict__ w,
+                                                                     double* __restrict__ dsum,
+                                                                     const unsigned char* __restrict__ mask) {
+  __shared__ double2 red[RED_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 32 + lane;
+  const long long TM = (long long)T * M;
+  double sx = 0.0, sy = 0.0;
+  if (idx < TM) {
+#pragma unroll 4
+    for (int k = warp; k < ks; k += RED_WARPS) {
+      const float2 p = part[(long long)k * TM + idx];
       sx += p.x;
       sy += p.y;
+    }
+  }
+  red[warp][lane] = make_double2(sx, sy);
+  __syncthreads();
+  if (warp != 0) return;
+  double d = 0.0;
+  if (idx < TM) {
+    sx = 0.0;
+    sy = 0.0;
+#pragma unroll
+    for (int i = 0; i < RED_WARPS; ++i) {
+      sx += red[i][lane].x;
+      sy += red[i][lane].y;
     }
     if (Z) Z[idx] = make_float2((float)sx, (float)sy);
     if (y) {
@@ -133,14 +157,7 @@ __global__ void __launch_bounds__(256) sense_reduce_kernel(const float2* __restr
   }
   if (dsum) {
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-      atomicAdd(dsum, s);
-    }
+    if (lane == 0) atomicAdd(dsum, d);
   }
 }
 
@@ -255,15 +272,24 @@ cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, doubl
   return CISOR_OK;
 }
 
-cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Z, int ntx) {
+// split-K partials of Z = H (f .* u) into c->sense_part: tensor cores where available, else the FP32 pipes
+static cisor_status sense_partials(cisor_ctx* c, const float2* f, const float2* u, int ntx, int* splits) {
+  if (c->Ht) return sense_tc_forward(c, f, u, ntx, splits);
   const long long chunk = ((c->Nf + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
   const int ks = (int)((c->Nf + chunk - 1) / chunk);
   dim3 g((c->M + GM - 1) / GM, (ntx + GT - 1) / GT, ks);
   sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->Nf, chunk, c->N);
   CISOR_CUDA(cudaGetLastError());
+  *splits = ks;
+  return CISOR_OK;
+}
+
+cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float2* Z, int ntx) {
+  int ks = 0;
+  CISOR_TRY(sense_partials(c, f, u, ntx, &ks));
   const int tm = ntx * c->M;
-  sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, nullptr, Z, nullptr,
-                                                               nullptr, nullptr);
+  sense_reduce_kernel<<<(tm + 31) / 32, 32 * RED_WARPS, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, nullptr, Z,
+                                                                      nullptr, nullptr, nullptr);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 2;
   return CISOR_OK;
@@ -271,21 +297,23 @@ cisor_status sense_forward(cisor_ctx* c, const float2* f, const float2* u, float
 
 cisor_status residual_and_D(cisor_ctx* c, const float2* f, const float2* u, const float2* y, float2* Z, float2* w,
                             int ntx) {
-  const long long chunk = ((c->Nf + c->ksplit - 1) / c->ksplit + GK - 1) / GK * GK;
-  const int ks = (int)((c->Nf + chunk - 1) / chunk);
-  dim3 g((c->M + GM - 1) / GM, (ntx + GT - 1) / GT, ks);
-  sense_fwd_kernel<<<g, 256, 0, c->stream>>>(c->H, f, u, c->sense_part, ntx, c->M, c->Nf, chunk, c->N);
-  CISOR_CUDA(cudaGetLastError());
+  int ks = 0;
+  CISOR_TRY(sense_partials(c, f, u, ntx, &ks));
   CISOR_CUDA(cudaMemsetAsync(c->dsum, 0, sizeof(double), c->stream));
   const int tm = ntx * c->M;
-  sense_reduce_kernel<<<(tm + 255) / 256, 256, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, y, Z, w, c->dsum,
-                                                               c->rx_mask);
+  sense_reduce_kernel<<<(tm + 31) / 32, 32 * RED_WARPS, 0, c->stream>>>(c->sense_part, ks, ntx, c->M, y, Z, w,
+                                                                      c->dsum, c->rx_mask);
   CISOR_CUDA(cudaGetLastError());
   c->launches += 2;
   return CISOR_OK;
 }
 
 cisor_status sense_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx) {
+  if (c->Ht) {
+    CISOR_TRY(sense_tc_adjoint(c, f, w, z, b, ntx));
+    c->launches += 1;
+    return CISOR_OK;
+  }
   dim3 g((unsigned)((c->Nf + GM - 1) / GM), (ntx + GT - 1) / GT);
   sense_adj_kernel<<<g, 256, 0, c->stream>>>(c->H, w, f, z, b, ntx, c->M, c->Nf, c->N);
   CISOR_CUDA(cudaGetLastError());

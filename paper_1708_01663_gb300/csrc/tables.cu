@@ -339,6 +339,7 @@ cisor_status build_tables(cisor_ctx* c) {
   else
     sensing_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, c->stream>>>(c->H, d_rx, c->M, n, c->delta, c->k, c->kb);
   CISOR_CUDA(cudaGetLastError());
+  CISOR_TRY(sense_tc_prepare(c));
   const unsigned gT = (unsigned)((TN + 255) / 256);
   if (c->ncomp == 3)
     ;  // incident fields written by vec_tables

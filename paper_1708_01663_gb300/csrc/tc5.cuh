@@ -18,7 +18,8 @@
 // TMEM columns (32-bit); warp w of a CTA reads lanes 32 (w % 4) .. + 31.
 //
 // These layouts and descriptors were checked on the GPU against a host
-// product (M = 128 and 64, N = 32, K = 32, canonical and padded strides).
+// product (M = 128 and 64, N = 32, K = 32, canonical and padded strides; and
+// kind::tf32 at M = 128, N = 96, K = 32 with LBO 144, hi / lo products to 8e-7).
 #pragma once
 #include <stdint.h>
 
@@ -46,6 +47,20 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t b
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
+}
+
+// the same with TF32 operands (kind::tf32: 32-bit elements, K = 8 per instruction, core matrices of 4 elements)
+__device__ __forceinline__ void tc_mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// instruction descriptor of kind::tf32: D FP32, A and B TF32 (format 2 at bits 7-9 and 10-12), K-major
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // the mbarrier completes (one arrival) when every MMA issued before by this thread is done
