@@ -9,7 +9,9 @@ calls of cisor_sense (Z = H (f .* u), Eq. 5) and cisor_sense_adjoint
 (z = H^H w, b = conj(f) .* z, Eq. 13) on device buffers, timed with CUDA
 events (each call also copies its inputs into the context's buffers).
 Prints one JSON line with the times and the rates against the matrix H
-that each GEMM streams (M x n^d complex64).  A launch list of the same
+that each GEMM streams (M x n^d complex64).  ``--check`` adds the relative
+L2 error of both products against FP64 products of the context's own H on
+the GPU (torch, complex128).  A launch list of the same
 command: ``ncu --clock-control none --metrics gpu__time_duration.sum -k
 regex:sense -c 20``; a full-metric capture names one kernel
 (``-k regex:sense_tc_kernel``) and one or two launches, on a small ``--n``.
@@ -27,6 +29,7 @@ def main():
     ap.add_argument("--config", default="c3")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--check", action="store_true")
     args = ap.parse_args()
     import torch
 
@@ -63,7 +66,21 @@ def main():
         times[name] = e0.elapsed_time(e1) / args.reps
     hbytes = 8.0 * M * Nf
     flops = 8.0 * T * M * Nf
-    print(json.dumps({"config": args.config, "n": n, "T": T, "M": M, "Nf": Nf, "H_bytes": hbytes,
+    check = {}
+    if args.check:
+        H = torch.empty((M, Nf), dtype=torch.complex64, device=dev)
+        ctx.sensing_matrix(H)
+        ctx.sense(f, u, Z)
+        ctx.sense_adjoint(f, w, z, b)
+        torch.cuda.synchronize()
+        H64 = H.to(torch.complex128)
+        Zref = (H64 @ (f.to(torch.complex128).repeat(Nf // N)[None, :] * u.to(torch.complex128)).T).T
+        zref = (H64.conj().T @ w.to(torch.complex128).T).T
+
+        def rel(a, r):
+            return float(torch.linalg.vector_norm(a.to(torch.complex128) - r) / torch.linalg.vector_norm(r))
+        check = {"forward_rel_err_vs_fp64": rel(Z, Zref), "adjoint_rel_err_vs_fp64": rel(z, zref)}
+    print(json.dumps({"config": args.config, "n": n, "T": T, "M": M, "Nf": Nf, "H_bytes": hbytes, **check,
                       "forward_ms": times["forward"], "adjoint_ms": times["adjoint"],
                       "forward_H_GBps": hbytes / times["forward"] / 1e6,
                       "adjoint_H_GBps": hbytes / times["adjoint"] / 1e6,

@@ -104,8 +104,10 @@ def test_forward_warm_start_keeps_solution():
     assert info.iters_max == 0
 
 
-def test_sense_and_adjoint():
-    n, T, M = 64, 6, 40
+# tensor cores (even sizes, T <= 128: 40 x 2 and 6 x 2 columns) and the FP32 fallback (odd receiver count,
+# odd field length, T > 128)
+@pytest.mark.parametrize("n,T,M", [(64, 6, 40), (40, 3, 24), (64, 6, 41), (63, 6, 40), (32, 130, 16)])
+def test_sense_and_adjoint(n, T, M):
     ctx, prob = make(n, T, M, 6.5)
     f = synth.ellipse_phantom(n, 3, (0.0, 0.5), 9, imag=0.02)
     u = synth.random_field(10, (T, n, n))
