@@ -1038,7 +1038,7 @@ __global__ void __launch_bounds__(NTH, 1) fno_proj_bwd(const float* __restrict__
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int j = 0; j < 4; ++j) adv[h][j][0] = adv[h][j][1] = adv[h][j][2] = adv[h][j][3] = 0.f;
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -1056,8 +1056,10 @@ __global__ void __launch_bounds__(NTH, 1) fno_proj_bwd(const float* __restrict__
             const int p = 16 * mt + g + (e >> 1) * 8, hl = 8 * nt + 2 * t + (e & 1), hid = 32 * q + hl;
             const float z = d[e] + c1[hid];
             const float dh = p2[hid] * ds[p] + p2[FH + hid] * ds[NPP + p];
-            hs[hl * NPP + p] = gelu_f(z);
-            zs[hl * NPP + p] = dh * gelu_grad_f(z);
+            float gv, gd;
+            gelu_and_grad(z, gv, gd);
+            hs[hl * NPP + p] = gv;
+            zs[hl * NPP + p] = dh * gd;
           }
         }
       }

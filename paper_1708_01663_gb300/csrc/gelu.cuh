@@ -57,4 +57,12 @@ __host__ __device__ __forceinline__ float gelu_grad_f(float x) {
   return fmaf(x * 0.39894228040143268f, gelu_exp(-0.5f * x * x), phi);
 }
 
+// both at once (one erf): g = gelu(x), gp = gelu'(x)
+__host__ __device__ __forceinline__ void gelu_and_grad(float x, float& g, float& gp) {
+  const float a = fabsf(x);
+  const float e = erf_pos(a * 0.70710678118654752f);
+  g = 0.5f * fmaf(a, e, x);
+  gp = fmaf(x * 0.39894228040143268f, gelu_exp(-0.5f * x * x), 0.5f * (1.f + copysignf(e, x)));
+}
+
 }  // namespace cisor
