@@ -43,6 +43,13 @@ typedef enum {
   CISOR_ERR_OOM = 4,           /* device allocation failed */
   CISOR_ERR_CUDA = 5           /* other CUDA error */
 } cisor_status;
+/* The sensing GEMMs (cisor_sense, cisor_sense_adjoint and every call that
+ * forms y, w or the gradient) run on the tensor cores when T <= 128 and M and
+ * the field length are even; their waits on the tensor cores are bounded.  A
+ * wait that gives up leaves a flag that the context reads without
+ * synchronising: the call that made it returns CISOR_ERR_CUDA if it had
+ * already waited for its stream (host outputs), else the next call on the
+ * context that does; the outputs since are invalid, the context stays usable. */
 
 typedef struct cisor_ctx cisor_ctx;
 

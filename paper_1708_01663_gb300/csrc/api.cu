@@ -65,11 +65,10 @@ struct Call {
     return CISOR_OK;
   }
   cisor_status leave() {
-    CISOR_TRY(sense_tc_check(c));
     CISOR_CUDA(cudaEventRecord(c->ev_b, c->stream));
     CISOR_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_b, 0));
     if (host_out) CISOR_CUDA(cudaStreamSynchronize(c->stream));
-    return CISOR_OK;
+    return sense_tc_check(c, host_out);
   }
 };
 
@@ -192,8 +191,7 @@ static void free_ctx(cisor_ctx* c) {
   void* dev[] = {c->ghat, c->tw, c->twst, c->H, c->u_in, c->R, c->r, c->rhat, c->p, c->v, c->s, c->tv, c->b, c->u,
                  c->vadj, c->z, c->gz, c->f, c->fz, c->grad, c->work_n, c->Y, c->w, c->yobs, c->sense_part,
                  c->part, c->scal, c->active, c->iters, c->txflag, c->dsum, c->sparams, c->tv_z,
-                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf, c->f_ck, c->Ht,
-                 c->tc_err};
+                 c->tv_r0, c->tv_r1, c->tv_p, c->rx_mask, c->tva0, c->tva1, c->vbuf, c->f_ck, c->Ht};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_active) cudaFreeHost(c->h_active);
@@ -358,9 +356,12 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
     int ks = c->ksplit;
     if (sense_tc_ok(c)) {  // tensor-core sensing: the transposed matrix, the timeout flag, its split-K partials
       ALLOC(c->Ht, (size_t)c->M * c->Nf * sizeof(float2));
-      ALLOC(c->tc_err, sizeof(int));
-      cudaError_t e = cudaMemset(c->tc_err, 0, sizeof(int));
-      if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset", __FILE__, __LINE__));
+      cudaError_t e = cudaHostAlloc((void**)&c->h_tc_err, sizeof(int), cudaHostAllocMapped);
+      if (e == cudaSuccess) {
+        *c->h_tc_err = 0;
+        e = cudaHostGetDevicePointer((void**)&c->tc_err, c->h_tc_err, 0);
+      }
+      if (e != cudaSuccess) return fail(cuda_fail(e, "mapped flag", __FILE__, __LINE__));
       st = sense_tc_setup(c);
       if (st != CISOR_OK) return fail(st);
       const int s = sense_tc_splits(c, nullptr);
@@ -386,7 +387,6 @@ cisor_status cisor_create(cisor_ctx** out, const cisor_geometry* g, void* stream
   {
     cudaError_t e = cudaMallocHost((void**)&c->h_active, sizeof(int) * c->T);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_dsum, sizeof(double) * 4);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_tc_err, sizeof(int));
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__));
   }
   st = conv_init(P);

@@ -59,13 +59,13 @@ cisor_status enter(cisor_batch* b) {
 
 // every problem stream -> caller's stream; synchronise when host memory was written
 cisor_status leave(cisor_batch* b, bool host_out) {
-  for (cisor_ctx* c : b->ctx) CISOR_TRY(sense_tc_check(c));
   for (cisor_ctx* c : b->ctx) {
     CISOR_CUDA(cudaEventRecord(c->ev_b, c->stream));
     CISOR_CUDA(cudaStreamWaitEvent(b->user_stream, c->ev_b, 0));
   }
   if (host_out)
     for (cisor_ctx* c : b->ctx) CISOR_CUDA(cudaStreamSynchronize(c->stream));
+  for (cisor_ctx* c : b->ctx) CISOR_TRY(sense_tc_check(c, host_out));
   return CISOR_OK;
 }
 

@@ -120,8 +120,8 @@ struct cisor_ctx {
   float2* sense_part;            // [ksplit, T, M]
   int ksplit;
   float2* Ht;                    // [Nf, M] transposed sensing matrix of the tensor-core adjoint (null: FP32 GEMMs)
-  int* tc_err;                   // set by a sensing kernel whose bounded wait on the tensor cores gave up
-  int* h_tc_err;                 // pinned copy of tc_err
+  int* tc_err;                   // device alias of h_tc_err
+  int* h_tc_err;                 // mapped host flag, set by a sensing kernel whose bounded MMA wait gave up
   bool tc_used;                  // a tensor-core sensing kernel ran in the current call
   int sms;                       // multiprocessors of the device
   int sense_tc_occ;              // resident CTAs per SM of the tensor-core forward sensing kernel
@@ -322,7 +322,7 @@ cisor_status sense_tc_setup(cisor_ctx* c);
 cisor_status sense_tc_prepare(cisor_ctx* c);
 cisor_status sense_tc_forward(cisor_ctx* c, const float2* f, const float2* u, int ntx, int* splits);
 cisor_status sense_tc_adjoint(cisor_ctx* c, const float2* f, const float2* w, float2* z, float2* b, int ntx);
-cisor_status sense_tc_check(cisor_ctx* c);
+cisor_status sense_tc_check(cisor_ctx* c, bool synced);
 cisor_status grad_assemble(cisor_ctx* c, const float2* u, const float2* gz, const float2* s, double gamma,
                            float2* grad, float2* zstep, int ntx);
 cisor_status gradient_step(cisor_ctx* c, const float2* s, const float2* g, double gamma, float2* z);

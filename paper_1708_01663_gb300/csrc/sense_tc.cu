@@ -39,6 +39,7 @@ constexpr int S_WAIT = 1 << 20;              // polls of the MMA completion barr
 // wave of 432-chunk CTAs (1.04 against 1.59 ms): CTAs that start together read the same slab of the small
 // operand, which then stays in L2 while H streams past it.
 constexpr long long S_KMAX = 64 * SK;
+constexpr long long S_MAX = 256;  // at most this many splits (partials T x M x 8 bytes each)
 
 
 __host__ __device__ constexpr int soff(int row, int k) {
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(STH, NB > 128 ? 1 : 2) sense_tc_kernel(const f
     ph ^= 1u;
     tc_fence_after();
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(err, 1);
+      if (tid == 0) *reinterpret_cast<volatile int*>(err) = 1;  // mapped host memory: a plain store
       failed = true;
     }
     return !failed;
@@ -281,6 +282,7 @@ int sense_tc_splits(const cisor_ctx* c, long long* KS) {
   if (S < 1) S = 1;
   long long ks = ((K + S - 1) / S + SK - 1) / SK * SK;
   if (ks > S_KMAX) ks = S_KMAX;
+  if ((K + ks - 1) / ks > S_MAX) ks = ((K + S_MAX - 1) / S_MAX + SK - 1) / SK * SK;  // bounds the partials
   if (KS) *KS = ks;
   return (int)((K + ks - 1) / ks);
 }
@@ -318,18 +320,20 @@ cisor_status sense_tc_adjoint(cisor_ctx* c, const float2* f, const float2* w, fl
   return CISOR_OK;
 }
 
-// after a call that ran the kernels above: an error if one of their waits on the tensor cores gave up
-cisor_status sense_tc_check(cisor_ctx* c) {
+// after a call that ran the kernels above: an error if one of their waits on the tensor cores gave up.  The
+// flag lives in mapped host memory, so reading it needs no synchronisation: synced = true when the call has
+// already waited for its stream (every kernel it launched has finished), else the flag stays armed and the next
+// call that synchronises reports a timeout of this one.
+cisor_status sense_tc_check(cisor_ctx* c, bool synced) {
   if (!c->tc_used) return CISOR_OK;
-  c->tc_used = false;
-  CISOR_CUDA(cudaMemcpyAsync(c->h_tc_err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CISOR_CUDA(cudaStreamSynchronize(c->stream));
-  if (*c->h_tc_err) {
-    CISOR_CUDA(cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
-    CISOR_CUDA(cudaStreamSynchronize(c->stream));
-    set_error("sensing: a wait on the tensor cores timed out; the outputs of this call are invalid");
+  volatile int* flag = c->h_tc_err;
+  if (*flag) {
+    *flag = 0;
+    c->tc_used = false;
+    set_error("sensing: a wait on the tensor cores timed out; the outputs of this or an earlier call are invalid");
     return CISOR_ERR_CUDA;
   }
+  if (synced) c->tc_used = false;
   return CISOR_OK;
 }
 
