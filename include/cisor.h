@@ -224,6 +224,14 @@ cisor_status cisor_launch_count(const cisor_ctx* ctx, long long* count);
  * output pointer may be NULL.  No GPU work is launched. */
 cisor_status cisor_device_info(int device, int* sm_count, int* max_clock_khz, int* fp32_lanes, int* cc);
 
+/* Self-test of the bounded waits of the tensor-core kernels (no counterpart
+ * in the paper; a diagnostic): one CTA on the current device takes tensor
+ * memory and waits at most `polls` (>= 1) polls on an mbarrier that it
+ * completes itself (arrive = 1) or that nothing completes (arrive = 0), frees
+ * the tensor memory and returns.  *completed (host) receives 1 if the wait
+ * completed, 0 if it gave up.  Synchronous (legacy default stream). */
+cisor_status cisor_tc_wait_selftest(int arrive, int polls, int* completed);
+
 /* Time `reps` back-to-back batched matvecs y_t = A x_t (adjoint = 0) or
  * A^H x_t (adjoint = 1) over all T transmitters of the context's workspace
  * (the FFT-convolution kernels of the field solves, Eq. 4), with CUDA events

@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "cisor_solve_iterations": [vp, c_int, POINTER(c_int), POINTER(c_int)],
         "cisor_launch_count": [vp, POINTER(c_longlong)],
         "cisor_device_info": [i, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)],
+        "cisor_tc_wait_selftest": [i, i, POINTER(c_int)],
         "cisor_time_matvec": [vp, vp, i, i, POINTER(c_double)],
         "cisor_apply_A_static": [vp, vp, vp, vp, i, i, i, i, vp],
         "cisor_data_term": [vp, vp, vp, POINTER(c_double), POINTER(SolveOpts), POINTER(SolveInfo)],
@@ -171,6 +172,13 @@ def device_info(device=0):
     v = [c_int() for _ in range(4)]
     _check(lib.cisor_device_info(int(device), *[ctypes.byref(x) for x in v]))
     return {"sm_count": v[0].value, "max_clock_khz": v[1].value, "fp32_lanes": v[2].value, "cc": v[3].value}
+
+
+def tc_wait_selftest(arrive, polls):
+    """Bounded tensor-core wait on the current device: True if the mbarrier completed within `polls` polls."""
+    v = c_int(-1)
+    _check(load().cisor_tc_wait_selftest(1 if arrive else 0, int(polls), ctypes.byref(v)))
+    return v.value == 1
 
 
 def apply_A_static(ghat_scaled, f, x, y, n, P, adjoint=False, stream=None):

@@ -338,3 +338,48 @@ cisor_status sense_tc_check(cisor_ctx* c, bool synced) {
 }
 
 }  // namespace cisor
+
+// ------------------------------------------------------------------ self-test of the bounded waits
+namespace cisor {
+// One CTA: warp 0 takes 32 TMEM columns, every thread waits at most `polls` polls on an mbarrier that thread 0
+// arrives on (arrive = 1) or that nothing completes (arrive = 0), the CTA agrees on the outcome, frees its
+// tensor memory and writes 1 (completed) or 0 (gave up) to *out.  The path every tensor-core kernel above
+// takes when its MMAs do not complete, without an MMA: nothing faults or hangs.
+__global__ void __launch_bounds__(128) tc_wait_selftest_kernel(int arrive, int polls, int* __restrict__ out) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) mbar_init(&mbar);
+  if (warp == 0) tmem_alloc(&tslot, 32);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&mbar)) : "memory");
+  const bool ok = mbar_wait(&mbar, 0, polls);
+  const bool all = !__syncthreads_or(!ok);
+  if (threadIdx.x == 0) *out = all ? 1 : 0;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tslot, 32);
+}
+}  // namespace cisor
+
+extern "C" cisor_status cisor_tc_wait_selftest(int arrive, int polls, int* completed) {
+  using namespace cisor;
+  if (!completed || polls < 1) {
+    set_error("cisor_tc_wait_selftest: NULL output or polls < 1");
+    return CISOR_ERR_INVALID_ARG;
+  }
+  int* d = nullptr;
+  CISOR_CUDA(cudaMalloc(&d, sizeof(int)));
+  cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) {
+    tc_wait_selftest_kernel<<<1, 128>>>(arrive ? 1 : 0, polls, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(completed, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "cisor_tc_wait_selftest", __FILE__, __LINE__);
+  return CISOR_OK;
+}

@@ -74,14 +74,15 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Waits for phase `parity` of the mbarrier, at most `limit` polls; false if it gave up.
+// Waits for phase `parity` of the mbarrier, at most `limit` polls of at most 1 us each (the suspend-time hint of
+// try_wait bounds how long one poll may keep the thread suspended); false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit) {
   uint32_t done = 0;
   for (int it = 0; it < limit && !done; ++it)
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(smem_addr(mbar)), "r"(parity)
+        : "r"(smem_addr(mbar)), "r"(parity), "r"(1000u)
         : "memory");
   return done != 0;
 }

@@ -83,3 +83,27 @@ def test_vectorial_fft_128(adjoint):
         op = prob.AH if adjoint else prob.A
         for t in range(2):
             assert rel(y[t], op(f, x[t])) < 2e-5, (n, t)
+
+
+def test_tensor_core_wait_gives_up_and_device_stays_usable():
+    """The bounded wait every tensor-core kernel takes on its MMA barrier: completes when the barrier does,
+    gives up after its poll limit when nothing completes it (no fault, no hang), and the device and a context
+    keep working afterwards."""
+    import time
+
+    build.build()
+    assert cisor.tc_wait_selftest(True, 1 << 20)
+    t0 = time.time()
+    assert not cisor.tc_wait_selftest(False, 2000)
+    assert time.time() - t0 < 10.0
+    assert cisor.tc_wait_selftest(True, 1 << 20)
+    n, T, M = 16, 2, 4
+    angles = synth.plane_wave_angles(T)
+    rx = synth.circle_receivers(M, 3.0)
+    ctx = cisor.Cisor(n, 1.0 / 8, angles, rx)
+    prob = model.Problem(n, 1.0 / 8, angles, rx, P=ctx.P)
+    f = synth.disk_phantom(n, 1.0 / 8, 0.5, 0.5 + 0.02j)
+    u = synth.random_field(4, (T, n, n))
+    Z = np.empty((T, M), np.complex64)
+    ctx.sense(c64(f), c64(u), Z)
+    assert rel(Z, prob.sense(f, u)) < 1e-5
